@@ -1,0 +1,24 @@
+"""Shared pytest configuration: the ``gpu`` marker and import paths.
+
+Tests marked ``gpu`` need a CUDA device and the compiled library; everything
+else runs on the CPU (oracle pins, host logic, C-ABI symbol checks, gloo).
+"""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled CUDA library")
+
+
+@pytest.fixture(scope="session")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
