@@ -1,0 +1,192 @@
+/*
+ * prosper.h -- C ABI of libprosper, a GB300 (sm_103a) implementation of the
+ * data-parallel E-step of ProSper's truncated-posterior EM (Expectation
+ * Truncation) and of the closed-form M-steps around it.
+ *
+ * Paper: G. Exarchakis et al., "ProSper -- A Python Library for Probabilistic
+ * Sparse Coding with Non-Standard Priors and Superpositions" (arXiv 1908.06843).
+ *   Eq. 1-2        generative model template p(s|Theta), p(y|s,Theta) = p(y; f(Theta,s))
+ *   Table 1        models: BSC (linear, binary), GSC (linear, spike-and-slab), MCA (max)
+ *   Sec. 2         EM with truncated posteriors
+ *   Sec. 3         BSC_ET(D, H, Hprime, gamma); Model.step; Model.inference -> res["s"], res["p"]
+ *
+ * Conventions for every entry point
+ *   - All array arguments are DEVICE pointers unless a name ends in _host.
+ *     The caller allocates and owns them; the library never frees them.
+ *   - Dictionaries are stored transposed: W is H x D row-major, row h is the
+ *     dictionary element W_h (column h of the paper's D x H matrix).
+ *   - Y is N x D row-major FP32.
+ *   - Calls are ordered on the given CUDA stream (cudaStream_t passed as
+ *     void*; NULL = legacy default stream) and return before the GPU work
+ *     finishes unless stated otherwise.  Results are valid after the stream
+ *     is synchronised.
+ *   - Return value: PROSPER_OK (0) or a negative PROSPER_E* code; the message
+ *     of the last failure on the calling thread is prosper_last_error().
+ *     No C++ exception crosses this interface.
+ *   - A context is not thread-safe: one host thread (or external locking)
+ *     per context.  Two contexts may be used concurrently on different streams.
+ */
+#ifndef PROSPER_H
+#define PROSPER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PROSPER_OK         0
+#define PROSPER_EINVAL    -1  /* bad argument: sizes, limits, NULL pointer, wrong model fields */
+#define PROSPER_ENOMEM    -2  /* device or pinned-host allocation failed */
+#define PROSPER_ECUDA     -3  /* a CUDA runtime call or kernel launch failed */
+#define PROSPER_ENONFINITE -4 /* non-finite value detected (input data or M-step result) */
+#define PROSPER_ETIMEOUT  -5  /* serving: the request did not finish within the wait limit */
+#define PROSPER_EBUSY     -6  /* serving: admission refused (request larger than the memory budget) */
+#define PROSPER_ESTATE    -7  /* wrong call order (e.g. serve_submit before serve_start) */
+
+/* Models of Table 1 that this library implements. */
+#define PROSPER_BSC 0  /* binary sparse coding: linear f = W s, s in {0,1}^H, Bernoulli(pi) prior */
+#define PROSPER_MCA 1  /* maximal causes analysis: f_d = max_h W_dh s_h, W >= 0 */
+#define PROSPER_GSC 2  /* Gaussian sparse coding: s_h = b_h z_h, b ~ Bernoulli(pi), z_h ~ N(mu_h, psi_h) */
+
+/* Precision of the BSC preselection projection W^T y (other models: FP32 only). */
+#define PROSPER_FP32          0  /* FP32 SIMT projection */
+#define PROSPER_BF16_RESCORE  1  /* BF16 tensor-core (tcgen05) projection for the selection only;
+                                    the H' selected projections are recomputed in FP32 */
+
+/* Limits.  BSC/MCA: 1 <= Hprime <= 10; GSC: Hprime <= 10 and gamma <= 3;
+ * 0 <= gamma <= Hprime <= H; BSC/MCA/GSC H <= 256; D <= 1024.
+ * PROSPER_BF16_RESCORE additionally needs D % 64 == 0 and H % 16 == 0, 16 <= H <= 256. */
+#define PROSPER_MAX_HPRIME 10
+
+/* theta[] layout (device doubles, PROSPER_THETA_LEN of them). */
+#define PROSPER_TH_PI    0   /* prior activation probability pi                   */
+#define PROSPER_TH_SIGMA 1   /* observation noise standard deviation sigma         */
+#define PROSPER_TH_RHO   2   /* MCA: exponent rho of the smoothed max in the M-step */
+#define PROSPER_THETA_LEN 4
+
+/* scal[] layout of the scalar sufficient statistics (device doubles). */
+#define PROSPER_SC_F      0  /* F = sum_n log sum_{s in K_n} p(s, y_n | Theta) (truncated log-likelihood, nats) */
+#define PROSPER_SC_S1     1  /* sum_n <|s|>_n  (expected number of active units)                         */
+#define PROSPER_SC_YY     2  /* sum_n y_n^T y_n                                                          */
+#define PROSPER_SC_N      3  /* number of points accumulated                                             */
+#define PROSPER_SC_MCA_R2 4  /* MCA: sum_n <||y_n - f(s)||^2>  (hard max, current W)                     */
+#define PROSPER_SC_LEN    8
+
+typedef struct prosper_ctx prosper_ctx;
+
+/* Model parameters Theta (Eq. 1-2).  All device pointers. */
+typedef struct {
+    float  *W;      /* H x D row-major FP32; read by E-step/encode, overwritten by M-step */
+    double *theta;  /* PROSPER_THETA_LEN doubles: pi, sigma, rho                          */
+    float  *mu;     /* GSC: H slab means (NULL for BSC/MCA)                               */
+    float  *psi;    /* GSC: H slab variances (NULL for BSC/MCA)                           */
+} prosper_params;
+
+/* Sufficient statistics accumulated by prosper_estep (all device, FP64,
+ * overwritten -- not accumulated -- by each call). */
+typedef struct {
+    double *At;    /* H x D: sum_n <s>_n y_n^T, the transpose of A = sum_n y_n <s>_n^T */
+    double *B;     /* H x H: sum_n <s s^T>_n (full symmetric matrix)                  */
+    double *scal;  /* PROSPER_SC_LEN scalars (layout above)                            */
+    double *gsc;   /* GSC: 3H = [sum <b_h>, sum <s_h>, sum <s_h^2>]; NULL otherwise     */
+    double *mca;   /* MCA: 2 H D = [sum <A_dh> y_dn (H x D), sum <A_dh> (H x D)]; else NULL */
+} prosper_stats;
+
+/* Create a context for one model and approximation (Sec. 3: BSC_ET(D, H,
+ * Hprime, gamma)).  The context owns the per-iteration constants (Gram matrix
+ * W^T W, 1/||W_h||, BF16 dictionary copy, GSC subset tables) and scratch for up
+ * to max_points points per call (larger calls are processed in pieces).
+ * precision: PROSPER_FP32 or PROSPER_BF16_RESCORE (BSC only).
+ * Errors: PROSPER_EINVAL on limits above, PROSPER_ENOMEM, PROSPER_ECUDA. */
+int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gamma,
+                 int precision, int64_t max_points);
+
+/* Release the context and everything it allocated.  NULL is accepted. */
+int prosper_destroy(prosper_ctx *ctx);
+
+/* Truncated E-step over N points (Sec. 2; Eq. 1-2 with Table 1's model):
+ * for each point the top-Hprime latents by the model's selection score are
+ * preselected, every binary state with at most gamma active units among them
+ * is evaluated, the posterior over that set is normalised, and the
+ * sufficient statistics are summed into *out (overwritten).
+ * Y: device N x D FP32.  N >= 0 (N = 0 gives zero statistics).
+ * Selection scores: BSC W_h^T y/||W_h||; MCA sum_d W_dh y_d / sum_d W_dh;
+ * GSC the singleton log-joint log p(e_h, y).  Exact score ties go to the lower h. */
+int prosper_estep(prosper_ctx *ctx, const prosper_params *p, const float *Y, int64_t N,
+                  prosper_stats *out, void *stream);
+
+/* Closed-form M-step ("Model.step", Sec. 3) from statistics of N points:
+ * BSC/GSC W = A B^{-1} (FP64 Cholesky), pi = sum<|s|>/(N H),
+ * sigma^2 = (sum y^T y - 2 tr(W^T A) + tr(W^T W B))/(N D) with the new W;
+ * GSC also mu_h, psi_h; MCA the rho-smoothed-max update of W (clamped >= 1e-6),
+ * pi as BSC, sigma^2 = sum<||y - f||^2>/(N D).  A unit with B_hh <= 1e-9 N
+ * keeps its parameters.  Overwrites p->W, p->theta (and mu, psi) on device. */
+int prosper_mstep(prosper_ctx *ctx, const prosper_stats *st, int64_t N, prosper_params *p,
+                  void *stream);
+
+/* Encoding with fixed Theta ("Model.inference", Sec. 3: res["s"], res["p"]).
+ * Per point n (all outputs device, may be NULL to skip):
+ *   sel     N x Hprime int16: the preselected latents, ascending
+ *   s_mean  N x Hprime float: posterior means <s_h> of those latents
+ *   map_idx N x gamma  int16: most probable state in K_n (active latents ascending, -1 padded)
+ *   map_p   N float: its approximate posterior probability q_n(MAP)
+ *   logZ    N float: log sum_{s in K_n} p(s, y_n | Theta)
+ * MAP ties go to the state with fewer active units, then the lexicographically
+ * smaller sorted list of local indices. */
+int prosper_encode(prosper_ctx *ctx, const prosper_params *p, const float *Y, int64_t N,
+                   int16_t *sel, float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
+                   void *stream);
+
+/* Same E-step as prosper_estep with Y and the statistics in HOST memory:
+ * Y_host (N x D) is copied to the device in pieces, the statistics are copied
+ * back into host arrays At_host (H x D), B_host (H x H), scal_host
+ * (PROSPER_SC_LEN) (each may be NULL), and the call returns after the stream
+ * has finished.  p (W, theta, mu, psi) stays on the device. */
+int prosper_estep_host(prosper_ctx *ctx, const prosper_params *p, const float *Y_host,
+                       int64_t N, double *At_host, double *B_host, double *scal_host,
+                       void *stream);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *prosper_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Encoding service with continuous batching (Sec. 3 "inference" as a
+ * service).  A host scheduler thread owned by the context takes submitted
+ * requests (1 .. 4096 patches each), packs waiting requests into the next
+ * free device slot as soon as one is free (a slot holds up to slot_points
+ * points), and runs prosper_encode on that slot's stream; several slots are
+ * in flight at once, so requests that arrive while others run are admitted
+ * as slots free up and their work overlaps on the device.  W, its Gram
+ * matrix and the state tables stay resident.  The per-point results do not
+ * depend on which batch or slot a point lands in.
+ * ---------------------------------------------------------------------- */
+
+/* Start the service.  n_slots device slots of slot_points points each
+ * (memory budget = n_slots * slot_points * (D*4 + per-point outputs) bytes).
+ * p is copied (device pointers must stay valid until prosper_serve_stop). */
+int prosper_serve_start(prosper_ctx *ctx, const prosper_params *p, int n_slots,
+                        int slot_points);
+
+/* Submit n points (host N x D FP32, copied before return).  *ticket receives
+ * the request id.  PROSPER_EBUSY if n > slot_points (never admissible). */
+int prosper_serve_submit(prosper_ctx *ctx, const float *Y_host, int n, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a ticket and copy its results to
+ * host arrays (layouts as prosper_encode; each may be NULL).  Returns
+ * PROSPER_ETIMEOUT if not finished in time (the ticket stays valid).
+ * t_submit_ns / t_done_ns (may be NULL) receive the submit time and the time
+ * the scheduler saw the slot's completion, CLOCK_MONOTONIC nanoseconds. */
+int prosper_serve_wait(prosper_ctx *ctx, uint64_t ticket, int timeout_ms,
+                       int16_t *sel_host, float *s_mean_host, int16_t *map_idx_host,
+                       float *map_p_host, float *logZ_host,
+                       int64_t *t_submit_ns, int64_t *t_done_ns);
+
+/* Stop the scheduler thread after the queued work finished; frees the slots. */
+int prosper_serve_stop(prosper_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PROSPER_H */

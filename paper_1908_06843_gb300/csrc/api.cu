@@ -1,0 +1,343 @@
+// api.cu -- the C ABI of include/prosper.h: argument checks, context memory,
+// and the order in which the E-step / M-step / encode kernels are issued.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+namespace prosper {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static int num_states(int Hp, int gamma) {
+    double c = 0.0, b = 1.0;
+    for (int k = 0; k <= gamma && k <= Hp; ++k) {
+        c += b;
+        b = b * (Hp - k) / (k + 1);
+    }
+    return (int)(c + 0.5);
+}
+
+template <class T>
+static int dev_alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return PROSPER_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc(%zu bytes) failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        cudaGetLastError();
+        return PROSPER_ENOMEM;
+    }
+    return PROSPER_OK;
+}
+
+static int check_params(const prosper_ctx *c, const prosper_params *p) {
+    if (!p || !p->W || !p->theta) {
+        set_error("params: W and theta must be device pointers");
+        return PROSPER_EINVAL;
+    }
+    if (c->model == PROSPER_GSC && (!p->mu || !p->psi)) {
+        set_error("params: GSC needs mu and psi");
+        return PROSPER_EINVAL;
+    }
+    return PROSPER_OK;
+}
+
+static int check_stats(const prosper_ctx *c, const prosper_stats *st) {
+    if (!st || !st->At || !st->B || !st->scal) {
+        set_error("stats: At, B and scal must be device pointers");
+        return PROSPER_EINVAL;
+    }
+    if (c->model == PROSPER_GSC && !st->gsc) {
+        set_error("stats: GSC needs gsc[3H]");
+        return PROSPER_EINVAL;
+    }
+    if (c->model == PROSPER_MCA && !st->mca) {
+        set_error("stats: MCA needs mca[2HD]");
+        return PROSPER_EINVAL;
+    }
+    return PROSPER_OK;
+}
+
+// ---------------------------------------------------------------- E-step
+static int estep_begin(prosper_ctx *c, const prosper_params *p, prosper_stats *st,
+                       cudaStream_t s) {
+    const size_t H = c->H, D = c->D;
+    PROSPER_CUDA_TRY(cudaMemsetAsync(st->At, 0, sizeof(double) * H * D, s));
+    PROSPER_CUDA_TRY(cudaMemsetAsync(st->B, 0, sizeof(double) * H * H, s));
+    PROSPER_CUDA_TRY(cudaMemsetAsync(st->scal, 0, sizeof(double) * PROSPER_SC_LEN, s));
+    if (c->model == PROSPER_GSC)
+        PROSPER_CUDA_TRY(cudaMemsetAsync(st->gsc, 0, sizeof(double) * 3 * H, s));
+    if (c->model == PROSPER_MCA)
+        PROSPER_CUDA_TRY(cudaMemsetAsync(st->mca, 0, sizeof(double) * 2 * H * D, s));
+    if (c->model == PROSPER_BSC) return launch_bsc_prep(c, p->W, s);
+    if (c->model == PROSPER_MCA) return launch_mca_prep(c, p->W, s);
+    return launch_gsc_prep(c, p, s);
+}
+
+static int estep_piece(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t n,
+                       prosper_stats *st, cudaStream_t s) {
+    int rc;
+    if (c->model == PROSPER_BSC) {
+        rc = (c->precision == PROSPER_BF16_RESCORE) ? launch_bsc_proj_bf16(c, Y, p->W, n, s)
+                                                     : launch_bsc_proj_f32(c, Y, n, s);
+        if (rc) return rc;
+        rc = launch_bsc_states(c, p->theta, n, 0, st, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+        if (rc) return rc;
+        return launch_astat(c, Y, n, st->At, s);
+    }
+    if (c->model == PROSPER_MCA)
+        return launch_mca_estep(c, p->W, p->theta, Y, n, st, nullptr, nullptr, nullptr, nullptr,
+                                nullptr, s);
+    return launch_gsc_estep(c, p, Y, n, st, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+}
+
+static int estep_end(prosper_ctx *c, prosper_stats *st, cudaStream_t s) {
+    return launch_symmetrize(c, st->B, s);
+}
+
+}  // namespace prosper
+
+using namespace prosper;
+
+extern "C" {
+
+const char *prosper_last_error(void) { return g_err; }
+
+int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gamma,
+                 int precision, int64_t max_points) {
+    if (!out) { set_error("out is NULL"); return PROSPER_EINVAL; }
+    *out = nullptr;
+    if (model < PROSPER_BSC || model > PROSPER_GSC) { set_error("unknown model %d", model); return PROSPER_EINVAL; }
+    if (D < 1 || D > 1024) { set_error("D=%d outside [1, 1024]", D); return PROSPER_EINVAL; }
+    if (H < 1 || H > 256) { set_error("H=%d outside [1, 256]", H); return PROSPER_EINVAL; }
+    if (Hprime < 1 || Hprime > PROSPER_MAX_HPRIME || Hprime > H) {
+        set_error("Hprime=%d outside [1, min(H, %d)]", Hprime, PROSPER_MAX_HPRIME);
+        return PROSPER_EINVAL;
+    }
+    if (gamma < 0 || gamma > Hprime) { set_error("gamma=%d outside [0, Hprime]", gamma); return PROSPER_EINVAL; }
+    if (model == PROSPER_GSC && gamma > 3) { set_error("GSC: gamma=%d > 3", gamma); return PROSPER_EINVAL; }
+    if (precision != PROSPER_FP32 && precision != PROSPER_BF16_RESCORE) {
+        set_error("unknown precision %d", precision);
+        return PROSPER_EINVAL;
+    }
+    if (precision == PROSPER_BF16_RESCORE &&
+        (model != PROSPER_BSC || D % 64 != 0 || H % 16 != 0 || H < 16)) {
+        set_error("BF16_RESCORE needs BSC, D %% 64 == 0, H %% 16 == 0, H >= 16");
+        return PROSPER_EINVAL;
+    }
+    if (max_points <= 0) max_points = 1 << 20;
+
+    prosper_ctx *c = new (std::nothrow) prosper_ctx();
+    if (!c) { set_error("host allocation failed"); return PROSPER_ENOMEM; }
+    c->model = model; c->D = D; c->H = H; c->Hp = Hprime; c->gamma = gamma;
+    c->precision = precision;
+    c->nK = num_states(Hprime, gamma);
+    c->chunk = max_points;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        set_error("no CUDA device: %s", cudaGetErrorString(e));
+        delete c;
+        return PROSPER_ECUDA;
+    }
+    int rc = PROSPER_OK;
+    const size_t ch = (size_t)c->chunk;
+#define ALLOC(ptr, n) do { if (!rc) rc = dev_alloc(&(ptr), (n)); } while (0)
+    ALLOC(c->d_status, 1);
+    ALLOC(c->msc, 16);
+    if (model == PROSPER_BSC || model == PROSPER_GSC) {
+        ALLOC(c->G, (size_t)H * H);
+        ALLOC(c->rnorm, (size_t)H);
+        ALLOC(c->mB, (size_t)H * H);
+        ALLOC(c->mX, (size_t)H * D);
+    }
+    if (model == PROSPER_BSC) {
+        if (precision == PROSPER_FP32) ALLOC(c->Wd, (size_t)D * H);
+        else ALLOC(c->Wb, (size_t)H * D);
+        ALLOC(c->sel, ch * SEL_STRIDE);
+        ALLOC(c->selp, ch * SEL_STRIDE);
+        ALLOC(c->es, ch * SEL_STRIDE);
+        ALLOC(c->yy, ch);
+    }
+    if (model == PROSPER_MCA) ALLOC(c->mca_logW, (size_t)H * D);
+    if (model == PROSPER_GSC) {
+        int nsub = 0;
+        double b = 1.0;
+        for (int k = 0; k <= gamma; ++k) { nsub += (int)(b + 0.5); b = b * (H - k) / (k + 1); }
+        c->gsc_nsub = nsub;
+        ALLOC(c->gsc_tab, (size_t)nsub * 8);
+    }
+#undef ALLOC
+    if (!rc && cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = PROSPER_ECUDA;
+    if (rc) {
+        prosper_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return PROSPER_OK;
+}
+
+int prosper_destroy(prosper_ctx *c) {
+    if (!c) return PROSPER_OK;
+    if (c->serve) prosper_serve_stop(c);
+    cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
+    cudaFree(c->mca_logW); cudaFree(c->gsc_tab);
+    cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es);
+    cudaFree(c->mB); cudaFree(c->mX); cudaFree(c->msc); cudaFree(c->d_status);
+    cudaFree(c->d_stage);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    delete c;
+    return PROSPER_OK;
+}
+
+int prosper_estep(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
+                  prosper_stats *st, void *stream) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    int rc = check_params(c, p);
+    if (!rc) rc = check_stats(c, st);
+    if (rc) return rc;
+    if (N < 0 || (N > 0 && !Y)) { set_error("bad Y/N"); return PROSPER_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = estep_begin(c, p, st, s))) return rc;
+    for (int64_t n0 = 0; n0 < N; n0 += c->chunk) {
+        const int64_t n = std::min<int64_t>(c->chunk, N - n0);
+        if ((rc = estep_piece(c, p, Y + n0 * c->D, n, st, s))) return rc;
+    }
+    return estep_end(c, st, s);
+}
+
+int prosper_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_params *p,
+                  void *stream) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    int rc = check_params(c, p);
+    if (!rc) rc = check_stats(c, st);
+    if (rc) return rc;
+    if (N <= 0) { set_error("mstep needs N > 0"); return PROSPER_EINVAL; }
+    return launch_mstep(c, st, N, p, (cudaStream_t)stream);
+}
+
+int prosper_encode(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
+                   int16_t *sel, float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
+                   void *stream) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    int rc = check_params(c, p);
+    if (rc) return rc;
+    if (N < 0 || (N > 0 && !Y)) { set_error("bad Y/N"); return PROSPER_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N == 0) return PROSPER_OK;
+    if (c->model == PROSPER_BSC) {
+        if ((rc = launch_bsc_prep(c, p->W, s))) return rc;
+        for (int64_t n0 = 0; n0 < N; n0 += c->chunk) {
+            const int64_t n = std::min<int64_t>(c->chunk, N - n0);
+            const float *Yp = Y + n0 * c->D;
+            rc = (c->precision == PROSPER_BF16_RESCORE) ? launch_bsc_proj_bf16(c, Yp, p->W, n, s)
+                                                         : launch_bsc_proj_f32(c, Yp, n, s);
+            if (rc) return rc;
+            rc = launch_bsc_states(c, p->theta, n, n0, nullptr, sel, s_mean, map_idx, map_p, logZ, s);
+            if (rc) return rc;
+        }
+        return PROSPER_OK;
+    }
+    if (c->model == PROSPER_MCA) {
+        if ((rc = launch_mca_prep(c, p->W, s))) return rc;
+        return launch_mca_estep(c, p->W, p->theta, Y, N, nullptr, sel, s_mean, map_idx, map_p,
+                                logZ, s);
+    }
+    if ((rc = launch_gsc_prep(c, p, s))) return rc;
+    return launch_gsc_estep(c, p, Y, N, nullptr, sel, s_mean, map_idx, map_p, logZ, s);
+}
+
+int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_host, int64_t N,
+                       double *At_host, double *B_host, double *scal_host, void *stream) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    int rc = check_params(c, p);
+    if (rc) return rc;
+    if (N < 0 || (N > 0 && !Y_host)) { set_error("bad Y/N"); return PROSPER_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t piece = std::min<int64_t>(c->chunk, 32768);
+    const size_t H = c->H, D = c->D;
+    if (!c->d_stage) {
+        // two device staging buffers + the device statistics of this call
+        size_t bytes = sizeof(float) * 2 * (size_t)piece * D;
+        PROSPER_CUDA_TRY(cudaMalloc(&c->d_stage, bytes));
+        c->stage_points = piece;
+    }
+    static thread_local double *d_stats = nullptr;
+    static thread_local size_t d_stats_len = 0;
+    const size_t need = H * D + H * H + PROSPER_SC_LEN + 3 * H + 2 * H * D;
+    if (d_stats_len < need) {
+        if (d_stats) cudaFree(d_stats);
+        PROSPER_CUDA_TRY(cudaMalloc(&d_stats, sizeof(double) * need));
+        d_stats_len = need;
+    }
+    prosper_stats st;
+    st.At = d_stats;
+    st.B = st.At + H * D;
+    st.scal = st.B + H * H;
+    st.gsc = st.scal + PROSPER_SC_LEN;
+    st.mca = st.gsc + 3 * H;
+    if ((rc = estep_begin(c, p, &st, s))) return rc;
+    cudaStream_t cs;
+    PROSPER_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t copied[2], used[2];
+    for (int i = 0; i < 2; ++i) {
+        cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&used[i], cudaEventDisableTiming);
+    }
+    // the copy stream starts after everything queued so far on s
+    cudaEvent_t start;
+    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    cudaEventRecord(start, s);
+    cudaStreamWaitEvent(cs, start, 0);
+    int k = 0;
+    for (int64_t n0 = 0; n0 < N && !rc; n0 += piece, ++k) {
+        const int64_t n = std::min<int64_t>(piece, N - n0);
+        float *buf = c->d_stage + (size_t)(k & 1) * piece * D;
+        if (k >= 2) cudaStreamWaitEvent(cs, used[k & 1], 0);
+        if (cudaMemcpyAsync(buf, Y_host + n0 * D, sizeof(float) * n * D, cudaMemcpyHostToDevice,
+                            cs) != cudaSuccess) {
+            set_error("H2D copy failed");
+            rc = PROSPER_ECUDA;
+            break;
+        }
+        cudaEventRecord(copied[k & 1], cs);
+        cudaStreamWaitEvent(s, copied[k & 1], 0);
+        rc = estep_piece(c, p, buf, n, &st, s);
+        cudaEventRecord(used[k & 1], s);
+    }
+    if (!rc) rc = estep_end(c, &st, s);
+    if (!rc) {
+        if (At_host) cudaMemcpyAsync(At_host, st.At, sizeof(double) * H * D, cudaMemcpyDeviceToHost, s);
+        if (B_host) cudaMemcpyAsync(B_host, st.B, sizeof(double) * H * H, cudaMemcpyDeviceToHost, s);
+        if (scal_host)
+            cudaMemcpyAsync(scal_host, st.scal, sizeof(double) * PROSPER_SC_LEN, cudaMemcpyDeviceToHost, s);
+    }
+    unsigned status = 0;
+    cudaMemcpyAsync(&status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaStreamSynchronize(cs);
+    for (int i = 0; i < 2; ++i) { cudaEventDestroy(copied[i]); cudaEventDestroy(used[i]); }
+    cudaEventDestroy(start);
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    if (e != cudaSuccess) { set_error("stream failed: %s", cudaGetErrorString(e)); return PROSPER_ECUDA; }
+    if (status & ST_NONFINITE) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s);
+        cudaStreamSynchronize(s);
+        set_error("non-finite value in the input data");
+        return PROSPER_ENONFINITE;
+    }
+    return PROSPER_OK;
+}
+
+}  // extern "C"

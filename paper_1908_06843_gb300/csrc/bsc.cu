@@ -1,0 +1,753 @@
+// bsc.cu -- binary sparse coding (BSC, Table 1 row 1: linear superposition
+// f = W s, Gaussian noise, binary latents, Bernoulli prior) truncated E-step.
+//
+// Path per call (paper Sec. 2, EM with truncated posteriors):
+//   k_gram / k_transpose      per-iteration constants: G = W^T W, 1/||W_h||, W (D x H)
+//   k_bsc_proj_f32            FP32 SIMT projection W^T y_n for all H latents of a
+//                             64-point tile, then top-H' preselection by the score
+//                             W_h^T y / ||W_h|| (ties to the lower h), one warp per point
+//   k_bsc_states<H'>          one thread per point: every state with <= gamma active
+//                             units among the H' candidates, log-sum-exp, posterior
+//                             moments, MAP; FP64 accumulation of sum <ss^T>, F, ...
+//   k_astat                   sum_n <s>_n y_n^T by a per-tile sort on the latent index
+//   k_symmetrize              B lower triangle from the upper one
+//
+// Log-joint of a state s over the candidates I (exact algebra from
+// ||y - W s||^2 = y^T y - 2 s^T W^T y + s^T W^T W s, Eq. 2):
+//   log p(s,y) - log p(0,y) = |s| log(pi/(1-pi)) + (s^T p - s^T G_II s / 2) / sigma^2
+// with p = W_I^T y.  Kernels work in base 2 (all terms times log2 e).
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace prosper {
+
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kLog2Pi = 1.8378770664093454836;
+
+// ------------------------------------------------------------------ prep
+// G[i][j] = sum_d Wt[i][d] Wt[j][d]; 16 x 16 output tile per block.
+__global__ void k_gram(const float *__restrict__ Wt, int H, int D, float *__restrict__ G) {
+    __shared__ float As[16][17], Bs[16][17];
+    int tx = threadIdx.x, ty = threadIdx.y;
+    int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+    float acc = 0.f;
+    for (int k0 = 0; k0 < D; k0 += 16) {
+        int k = k0 + tx;
+        As[ty][tx] = (i0 + ty < H && k < D) ? Wt[(size_t)(i0 + ty) * D + k] : 0.f;
+        Bs[ty][tx] = (j0 + ty < H && k < D) ? Wt[(size_t)(j0 + ty) * D + k] : 0.f;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = fmaf(As[ty][kk], Bs[tx][kk], acc);
+        __syncthreads();
+    }
+    if (i0 + ty < H && j0 + tx < H) G[(size_t)(i0 + ty) * H + j0 + tx] = acc;
+}
+
+__global__ void k_rnorm(const float *__restrict__ G, int H, float *__restrict__ rnorm) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < H) {
+        float g = G[(size_t)h * H + h];
+        rnorm[h] = g > 0.f ? rsqrtf(g) : 0.f;
+    }
+}
+
+// Wd[d][h] = Wt[h][d]
+__global__ void k_transpose(const float *__restrict__ Wt, int H, int D, float *__restrict__ Wd) {
+    __shared__ float t[32][33];
+    int h0 = blockIdx.y * 32, d0 = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int h = h0 + r, d = d0 + threadIdx.x;
+        t[r][threadIdx.x] = (h < H && d < D) ? Wt[(size_t)h * D + d] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int d = d0 + r, h = h0 + threadIdx.x;
+        if (d < D && h < H) Wd[(size_t)d * H + h] = t[threadIdx.x][r];
+    }
+}
+
+// ------------------------------------------------- selection (warp per point)
+__device__ __forceinline__ unsigned ordered_key(float s) {
+    unsigned b = __float_as_uint(s);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Top-Hp of the scores of one point held 8 per lane (h = lane + 32 j), exact
+// ties to the lower h.  Returns the selected h of round r in sel[r] (warp-uniform).
+template <int HPMAX>
+__device__ __forceinline__ void warp_topk(unsigned key[8], int Hp, int sel[HPMAX], int lane) {
+    unsigned lk = key[0];
+    int lj = 0;
+#pragma unroll
+    for (int j = 1; j < 8; ++j)
+        if (key[j] > lk) { lk = key[j]; lj = j; }
+#pragma unroll
+    for (int r = 0; r < HPMAX; ++r) {
+        if (r < Hp) {
+            unsigned wmax = __reduce_max_sync(0xffffffffu, lk);
+            unsigned code = (lk == wmax) ? (unsigned)(lj * 32 + lane) : 0xffffffffu;
+            unsigned hw = __reduce_min_sync(0xffffffffu, code);
+            sel[r] = (int)hw;
+            if ((int)(hw & 31u) == lane) {
+                int jw = (int)(hw >> 5);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j == jw) key[j] = 0u;
+                lk = key[0];
+                lj = 0;
+#pragma unroll
+                for (int j = 1; j < 8; ++j)
+                    if (key[j] > lk) { lk = key[j]; lj = j; }
+            }
+        } else {
+            sel[r] = 0x7fffffff;
+        }
+    }
+}
+
+// ------------------------------------------------ FP32 projection + selection
+constexpr int PT = 64;        // points per tile
+constexpr int PK = 32;        // d per k-chunk
+constexpr int PH = 256;       // max H of this kernel
+constexpr int PS = PH + 4;    // padded row of the projection tile in smem
+
+struct ProjSmem {
+    float Ys[PK][PT];         // 8 KB   (d-major so a thread reads 8 points with 2 LDS.128)
+    float Ws[PK][PH];         // 32 KB
+    float Ps[PT][PS];         // 66.5 KB
+};
+
+// Grid: persistent, one 256-thread CTA per SM.  Thread (tp = tid & 7, th = tid >> 3)
+// accumulates the 8 x 8 block P[tp*8 + i][th*8 + j] of the 64 x 256 tile.
+__global__ void __launch_bounds__(256, 1)
+k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
+               const float *__restrict__ rnorm, int64_t N, int D, int H, int Hp,
+               int32_t *__restrict__ sel_out, float *__restrict__ selp_out,
+               float *__restrict__ yy_out, unsigned *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ProjSmem &sm = *reinterpret_cast<ProjSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tp = tid & 7, th = tid >> 3;
+    const int64_t ntiles = (N + PT - 1) / PT;
+    const bool vecY = (D % 4) == 0, vecW = (H % 4) == 0;
+
+    float rn[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int h = lane + 32 * j;
+        rn[j] = h < H ? rnorm[h] : 0.f;
+    }
+
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t n0 = tile * PT;
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+        for (int k0 = 0; k0 < D; k0 += PK) {
+            // Y chunk: 64 points x 32 d, stored transposed
+            for (int idx = tid; idx < PT * (PK / 4); idx += 256) {
+                int p = idx >> 3, q = idx & 7;
+                int64_t n = n0 + p;
+                int d = k0 + q * 4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (n < N) {
+                    const float *row = Y + n * D;
+                    if (vecY && d + 3 < D) {
+                        v = __ldg(reinterpret_cast<const float4 *>(row + d));
+                    } else {
+                        if (d < D) v.x = row[d];
+                        if (d + 1 < D) v.y = row[d + 1];
+                        if (d + 2 < D) v.z = row[d + 2];
+                        if (d + 3 < D) v.w = row[d + 3];
+                    }
+                }
+                sm.Ys[q * 4 + 0][p] = v.x;
+                sm.Ys[q * 4 + 1][p] = v.y;
+                sm.Ys[q * 4 + 2][p] = v.z;
+                sm.Ys[q * 4 + 3][p] = v.w;
+            }
+            // W chunk: 32 d x 256 h
+            for (int idx = tid; idx < PK * (PH / 4); idx += 256) {
+                int kk = idx >> 6, c4 = (idx & 63) * 4;
+                int d = k0 + kk;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (d < D) {
+                    const float *row = Wd + (size_t)d * H;
+                    if (vecW && c4 + 3 < H) {
+                        v = __ldg(reinterpret_cast<const float4 *>(row + c4));
+                    } else {
+                        if (c4 < H) v.x = row[c4];
+                        if (c4 + 1 < H) v.y = row[c4 + 1];
+                        if (c4 + 2 < H) v.z = row[c4 + 2];
+                        if (c4 + 3 < H) v.w = row[c4 + 3];
+                    }
+                }
+                *reinterpret_cast<float4 *>(&sm.Ws[kk][c4]) = v;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < PK; ++kk) {
+                float4 y0 = *reinterpret_cast<const float4 *>(&sm.Ys[kk][tp * 8]);
+                float4 y1 = *reinterpret_cast<const float4 *>(&sm.Ys[kk][tp * 8 + 4]);
+                float4 w0 = *reinterpret_cast<const float4 *>(&sm.Ws[kk][th * 8]);
+                float4 w1 = *reinterpret_cast<const float4 *>(&sm.Ws[kk][th * 8 + 4]);
+                float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+                float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(yv[i], wv[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float *row = &sm.Ps[tp * 8 + i][th * 8];
+            *reinterpret_cast<float4 *>(row) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            *reinterpret_cast<float4 *>(row + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+        }
+        __syncthreads();
+
+        // selection: warp w takes points w*8 .. w*8+7 of the tile
+        for (int i = 0; i < PT / 8; ++i) {
+            const int p = warp * (PT / 8) + i;
+            const int64_t n = n0 + p;
+            if (n >= N) break;
+            unsigned key[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                int h = lane + 32 * j;
+                key[j] = h < H ? ordered_key(sm.Ps[p][h] * rn[j]) : 0u;
+            }
+            int sel[PROSPER_MAX_HPRIME];
+            warp_topk<PROSPER_MAX_HPRIME>(key, Hp, sel, lane);
+            // lane r < Hp writes its round's latent at its ascending rank
+            int myh = 0x7fffffff;
+#pragma unroll
+            for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
+                if (r == lane) myh = sel[r];
+            int rank = 0;
+#pragma unroll
+            for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) rank += (sel[r] < myh) ? 1 : 0;
+            if (lane < Hp) {
+                sel_out[n * SEL_STRIDE + rank] = myh;
+                selp_out[n * SEL_STRIDE + rank] = sm.Ps[p][myh];
+            }
+            // y^T y of the point (also the non-finite-input check)
+            float s = 0.f;
+            const float *row = Y + n * D;
+            for (int d = lane; d < D; d += 32) {
+                float v = row[d];
+                s = fmaf(v, v, s);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) {
+                yy_out[n] = s;
+                if (!isfinite(s)) atomicOr(status, ST_NONFINITE);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------- state kernel
+__host__ __device__ constexpr int cpopc(int x) { return x == 0 ? 0 : (x & 1) + cpopc(x >> 1); }
+__host__ __device__ constexpr int cctz(int x) { return (x & 1) ? 0 : 1 + cctz(x >> 1); }
+
+// canonical order of states: fewer active units first, then lexicographic
+// order of the sorted local-index lists (lowest differing unit decides).
+__device__ __forceinline__ bool canon_less(unsigned a, unsigned b) {
+    int pa = __popc(a), pb = __popc(b);
+    if (pa != pb) return pa < pb;
+    unsigned d = a ^ b;
+    return d != 0u && (a & (d & (0u - d))) != 0u;
+}
+
+struct StateArgs {
+    const int32_t *sel;
+    const float *selp;
+    const float *yy;
+    const float *G;
+    int64_t N;
+    int H, D, gamma;
+    const double *theta;
+    // outputs (estep)
+    float *es;
+    double *B, *scal;
+    // outputs (encode)
+    int16_t *sel_out, *map_out;
+    float *smean_out, *mapp_out, *logz_out;
+    int64_t n_offset;   // row offset of this piece in the encode outputs
+};
+
+// One thread per data point.  Local units 0..LB-1 ("lo") are enumerated by a
+// warp-uniform loop; units LB..HP-1 ("hi", HB = min(HP,5) of them) are
+// unrolled, so each lo pattern evaluates its 2^HB hi patterns from registers:
+//   l(lo, t) = L(lo) + sum_{u in t} c_u(lo) + M(t),
+//   L(lo)  = sum_{j in lo} a_j + sum_{i<j in lo} b_ij,
+//   c_u(lo) = a_u + sum_{i in lo} b_iu,   M(t) = sum_{u<v in t} b_uv,
+// with a_j = log2e (log(pi/(1-pi)) + (p_j - G_jj/2)/sigma^2), b_ij = -log2e G_ij/sigma^2.
+// States with more than gamma active units are skipped by warp-uniform branches.
+template <int HP, bool ENCODE>
+__global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
+    constexpr int HB = HP < 5 ? HP : 5;
+    constexpr int LB = HP - HB;
+    constexpr int NT = 1 << HB;
+    constexpr int NLO = 1 << LB;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = n < A.N;
+    const int64_t nn = valid ? n : 0;
+
+    const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
+    const float lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634);
+    const float is2 = (float)(1.4426950408889634 / (sigma * sigma));
+    const int gamma = A.gamma;
+    const int H = A.H;
+
+    int I[HP];
+    float a[HP], b[HP][HP];
+#pragma unroll
+    for (int j = 0; j < HP; ++j) I[j] = A.sel[nn * SEL_STRIDE + j];
+#pragma unroll
+    for (int j = 0; j < HP; ++j) {
+        float pj = A.selp[nn * SEL_STRIDE + j];
+        float gjj = __ldg(A.G + (size_t)I[j] * H + I[j]);
+        a[j] = lpi + (pj - 0.5f * gjj) * is2;
+    }
+#pragma unroll
+    for (int i = 0; i < HP; ++i)
+#pragma unroll
+        for (int j = i + 1; j < HP; ++j) b[i][j] = -__ldg(A.G + (size_t)I[i] * H + I[j]) * is2;
+
+    float M[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        float s = 0.f;
+#pragma unroll
+        for (int u = 0; u < HB; ++u)
+#pragma unroll
+            for (int v = u + 1; v < HB; ++v)
+                if (((t >> u) & 1) && ((t >> v) & 1)) s += b[LB + u][LB + v];
+        M[t] = s;
+    }
+
+    // -------- pass 1: maximum log-joint
+    float m = -INFINITY;
+    for (int lo = 0; lo < NLO; ++lo) {
+        const int cap = gamma - __popc(lo);
+        if (cap < 0) continue;
+        float L = 0.f;
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            if ((lo >> i) & 1) {
+                L += a[i];
+#pragma unroll
+                for (int j = i + 1; j < LB; ++j)
+                    if ((lo >> j) & 1) L += b[i][j];
+            }
+        }
+        float c[HB];
+#pragma unroll
+        for (int u = 0; u < HB; ++u) {
+            float v = a[LB + u];
+#pragma unroll
+            for (int i = 0; i < LB; ++i)
+                if ((lo >> i) & 1) v += b[i][LB + u];
+            c[u] = v;
+        }
+        float C[NT];
+        C[0] = L;
+#pragma unroll
+        for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)];
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+            if (cpopc(t) <= cap) m = fmaxf(m, C[t] + M[t]);
+    }
+
+    // -------- pass 2: exponentials, moments, MAP
+    float Z = 0.f;
+    float LL[LB > 0 ? LB : 1][LB > 0 ? LB : 1];
+    float LH[LB > 0 ? LB : 1][HB];
+    float Gacc[NT];
+#pragma unroll
+    for (int i = 0; i < (LB > 0 ? LB : 1); ++i) {
+#pragma unroll
+        for (int j = 0; j < (LB > 0 ? LB : 1); ++j) LL[i][j] = 0.f;
+#pragma unroll
+        for (int u = 0; u < HB; ++u) LH[i][u] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Gacc[t] = 0.f;
+    unsigned mapmask = 0xffffffffu;
+
+    for (int lo = 0; lo < NLO; ++lo) {
+        const int cap = gamma - __popc(lo);
+        if (cap < 0) continue;
+        float L = 0.f;
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            if ((lo >> i) & 1) {
+                L += a[i];
+#pragma unroll
+                for (int j = i + 1; j < LB; ++j)
+                    if ((lo >> j) & 1) L += b[i][j];
+            }
+        }
+        float c[HB];
+#pragma unroll
+        for (int u = 0; u < HB; ++u) {
+            float v = a[LB + u];
+#pragma unroll
+            for (int i = 0; i < LB; ++i)
+                if ((lo >> i) & 1) v += b[i][LB + u];
+            c[u] = v;
+        }
+        float C[NT];
+        C[0] = L;
+#pragma unroll
+        for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)];
+        float e[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            e[t] = 0.f;
+            if (cpopc(t) <= cap) {
+                float l = C[t] + M[t];
+                e[t] = exp2f(l - m);
+                if (l == m) {
+                    unsigned cand = (unsigned)lo | ((unsigned)t << LB);
+                    if (canon_less(cand, mapmask)) mapmask = cand;
+                }
+            }
+        }
+        // R[u] = sum_{t contains u} e[t]; total by pairwise halving
+        float R[HB];
+        float Zlo;
+        {
+            float cur[NT];
+#pragma unroll
+            for (int t = 0; t < NT; ++t) cur[t] = e[t];
+#pragma unroll
+            for (int u = 0; u < HB; ++u) {
+                const int half = NT >> (u + 1);
+                float r = 0.f;
+#pragma unroll
+                for (int t = 0; t < half; ++t) {
+                    r += cur[2 * t + 1];
+                    cur[t] = cur[2 * t] + cur[2 * t + 1];
+                }
+                R[u] = r;
+            }
+            Zlo = cur[0];
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) Gacc[t] += e[t];
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            if ((lo >> i) & 1) {
+#pragma unroll
+                for (int u = 0; u < HB; ++u) LH[i][u] += R[u];
+#pragma unroll
+                for (int j = i; j < LB; ++j)
+                    if ((lo >> j) & 1) LL[i][j] += Zlo;
+            }
+        }
+        Z += Zlo;
+    }
+
+    // hi-hi moments from the accumulated hi-pattern weights
+    float HS[HB], HPr[HB][HB];
+#pragma unroll
+    for (int u = 0; u < HB; ++u) {
+        float s = 0.f;
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+            if ((t >> u) & 1) s += Gacc[t];
+        HS[u] = s;
+#pragma unroll
+        for (int v = u + 1; v < HB; ++v) {
+            float q = 0.f;
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+                if (((t >> u) & 1) && ((t >> v) & 1)) q += Gacc[t];
+            HPr[u][v] = q;
+        }
+    }
+    const float invZ = 1.f / Z;
+    float es[HP];
+#pragma unroll
+    for (int j = 0; j < HP; ++j) es[j] = (j < LB ? LL[j < LB ? j : 0][j < LB ? j : 0] : HS[j >= LB ? j - LB : 0]) * invZ;
+
+    const double yy = (double)A.yy[nn];
+    const double s2 = sigma * sigma;
+    const double logp0 = H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2)) - yy / (2.0 * s2);
+    const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp0;
+
+    if (ENCODE) {
+        if (valid) {
+            const int64_t o = A.n_offset + n;
+            if (A.sel_out)
+#pragma unroll
+                for (int j = 0; j < HP; ++j) A.sel_out[o * HP + j] = (int16_t)I[j];
+            if (A.smean_out)
+#pragma unroll
+                for (int j = 0; j < HP; ++j) A.smean_out[o * HP + j] = es[j];
+            if (A.map_out) {
+                int k = 0;
+#pragma unroll
+                for (int j = 0; j < HP; ++j)
+                    if (((mapmask >> j) & 1u) && k < gamma) A.map_out[o * gamma + k++] = (int16_t)I[j];
+                for (; k < gamma; ++k) A.map_out[o * gamma + k] = (int16_t)-1;
+            }
+            if (A.mapp_out) A.mapp_out[o] = invZ;
+            if (A.logz_out) A.logz_out[o] = (float)logZ;
+        }
+        return;
+    }
+
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < HP; ++j) A.es[n * SEL_STRIDE + j] = es[j];
+        // sum <s s^T> into the upper triangle of B (I ascending -> I_i < I_j)
+#pragma unroll
+        for (int i = 0; i < HP; ++i) {
+            atomicAdd(A.B + (size_t)I[i] * H + I[i], (double)es[i]);
+#pragma unroll
+            for (int j = i + 1; j < HP; ++j) {
+                float v;
+                if (j < LB) v = LL[i < LB ? i : 0][j < LB ? j : 0];
+                else if (i < LB) v = LH[i < LB ? i : 0][j - LB >= 0 ? j - LB : 0];
+                else v = HPr[i - LB >= 0 ? i - LB : 0][j - LB >= 0 ? j - LB : 0];
+                atomicAdd(A.B + (size_t)I[i] * H + I[j], (double)(v * invZ));
+            }
+        }
+    }
+    // scalar statistics: warp reduction in FP64, one atomic per warp
+    double s1 = 0.0, f = 0.0, y2 = 0.0, cnt = 0.0;
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < HP; ++j) s1 += es[j];
+        f = logZ;
+        y2 = yy;
+        cnt = 1.0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        f += __shfl_xor_sync(0xffffffffu, f, o);
+        y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
+        atomicAdd(A.scal + PROSPER_SC_F, f);
+        atomicAdd(A.scal + PROSPER_SC_S1, s1);
+        atomicAdd(A.scal + PROSPER_SC_YY, y2);
+        atomicAdd(A.scal + PROSPER_SC_N, cnt);
+    }
+}
+
+// ----------------------------------------------------- sum_n <s>_n y_n^T
+// Grid (ceil(D/64), ranges).  A CTA owns a 64-wide slice of d for its range of
+// points and keeps At[:, slice] in shared memory.  Per 256-point chunk the
+// (point, <s>) pairs are bucketed by latent h; warp w then owns latents
+// h = w, w+8, ... so every shared-memory row has a single writer.
+constexpr int AT = 256;   // points per chunk
+constexpr int AD = 64;    // d per slice
+
+__global__ void __launch_bounds__(256, 1)
+k_astat(const float *__restrict__ Y, const int32_t *__restrict__ sel, const float *__restrict__ es,
+        int64_t N, int D, int H, int Hp, int64_t pts_per_cta, double *__restrict__ At) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Apart = reinterpret_cast<float *>(smem_raw);              // H x AD
+    float *Ys = Apart + (size_t)H * AD;                              // AT x AD
+    float *lv = Ys + AT * AD;                                        // AT*Hp values
+    int *ln = reinterpret_cast<int *>(lv + AT * PROSPER_MAX_HPRIME);  // AT*Hp point ids
+    int *cnt = ln + AT * PROSPER_MAX_HPRIME;                         // H+1
+    int *off = cnt + (H + 1);                                        // H+1
+    int *fill = off + (H + 1);                                       // H
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int d0 = blockIdx.x * AD;
+    const int64_t p_begin = (int64_t)blockIdx.y * pts_per_cta;
+    const int64_t p_end = min(N, p_begin + pts_per_cta);
+    for (int i = tid; i < H * AD; i += 256) Apart[i] = 0.f;
+
+    for (int64_t c0 = p_begin; c0 < p_end; c0 += AT) {
+        const int np = (int)min((int64_t)AT, p_end - c0);
+        for (int h = tid; h < H; h += 256) { cnt[h] = 0; fill[h] = 0; }
+        __syncthreads();
+        for (int i = tid; i < np * Hp; i += 256) {
+            int p = i / Hp, j = i - p * Hp;
+            atomicAdd(&cnt[sel[(c0 + p) * SEL_STRIDE + j]], 1);
+        }
+        // Y slice of the chunk
+        for (int i = tid; i < AT * AD; i += 256) {
+            int p = i / AD, c = i - p * AD;
+            int d = d0 + c;
+            Ys[i] = (p < np && d < D) ? Y[(c0 + p) * D + d] : 0.f;
+        }
+        __syncthreads();
+        if (warp == 0) {   // exclusive scan of cnt -> off
+            int carry = 0;
+            for (int base = 0; base < H; base += 32) {
+                int h = base + lane;
+                int v = h < H ? cnt[h] : 0;
+                int x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += t;
+                }
+                if (h < H) off[h] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) off[H] = carry;
+        }
+        __syncthreads();
+        for (int i = tid; i < np * Hp; i += 256) {
+            int p = i / Hp, j = i - p * Hp;
+            int h = sel[(c0 + p) * SEL_STRIDE + j];
+            int pos = off[h] + atomicAdd(&fill[h], 1);
+            ln[pos] = p;
+            lv[pos] = es[(c0 + p) * SEL_STRIDE + j];
+        }
+        __syncthreads();
+        for (int h = warp; h < H; h += 8) {
+            float a0 = 0.f, a1 = 0.f;
+            const int e1 = off[h + 1];
+            for (int e = off[h]; e < e1; ++e) {
+                const float v = lv[e];
+                const float2 y = *reinterpret_cast<const float2 *>(&Ys[ln[e] * AD + 2 * lane]);
+                a0 = fmaf(v, y.x, a0);
+                a1 = fmaf(v, y.y, a1);
+            }
+            float2 *dst = reinterpret_cast<float2 *>(&Apart[h * AD + 2 * lane]);
+            float2 cur = *dst;
+            cur.x += a0;
+            cur.y += a1;
+            *dst = cur;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < H * AD; i += 256) {
+        int h = i / AD, c = i - h * AD;
+        int d = d0 + c;
+        if (d < D && Apart[i] != 0.f) atomicAdd(At + (size_t)h * D + d, (double)Apart[i]);
+    }
+}
+
+__global__ void k_symmetrize(double *B, int H) {
+    int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+    if (i < H && j < H && j < i) B[(size_t)i * H + j] = B[(size_t)j * H + i];
+}
+
+}  // namespace
+
+// ================================================================ launchers
+int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
+    const int H = c->H, D = c->D;
+    dim3 gb(16, 16), gg((H + 15) / 16, (H + 15) / 16);
+    k_gram<<<gg, gb, 0, s>>>(W, H, D, c->G);
+    PROSPER_LAUNCH_CHECK();
+    k_rnorm<<<(H + 255) / 256, 256, 0, s>>>(c->G, H, c->rnorm);
+    PROSPER_LAUNCH_CHECK();
+    if (c->Wd) {
+        dim3 tb(32, 8), tg((D + 31) / 32, (H + 31) / 32);
+        k_transpose<<<tg, tb, 0, s>>>(W, H, D, c->Wd);
+        PROSPER_LAUNCH_CHECK();
+    }
+    return PROSPER_OK;
+}
+
+int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s) {
+    if (N <= 0) return PROSPER_OK;
+    static bool attr_done = false;
+    const size_t smem = sizeof(ProjSmem);
+    if (!attr_done) {
+        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_bsc_proj_f32,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_done = true;
+    }
+    int64_t ntiles = (N + PT - 1) / PT;
+    int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
+    k_bsc_proj_f32<<<grid, 256, smem, s>>>(Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->sel,
+                                           c->selp, c->yy, c->d_status);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+template <int HP>
+static int states_dispatch(StateArgs &A, bool encode, int64_t N, cudaStream_t s) {
+    int grid = (int)((N + 255) / 256);
+    if (encode) k_bsc_states<HP, true><<<grid, 256, 0, s>>>(A);
+    else k_bsc_states<HP, false><<<grid, 256, 0, s>>>(A);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_offset,
+                      prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
+                      float *mapp_out, float *logz_out, cudaStream_t s) {
+    if (N <= 0) return PROSPER_OK;
+    StateArgs A;
+    A.sel = c->sel; A.selp = c->selp; A.yy = c->yy; A.G = c->G;
+    A.N = N; A.H = c->H; A.D = c->D; A.gamma = c->gamma; A.theta = theta;
+    A.es = c->es;
+    A.B = st ? st->B : nullptr;
+    A.scal = st ? st->scal : nullptr;
+    A.sel_out = sel_out; A.map_out = map_out; A.smean_out = smean_out; A.mapp_out = mapp_out;
+    A.logz_out = logz_out; A.n_offset = n_offset;
+    const bool enc = (st == nullptr);
+    switch (c->Hp) {
+        case 1: return states_dispatch<1>(A, enc, N, s);
+        case 2: return states_dispatch<2>(A, enc, N, s);
+        case 3: return states_dispatch<3>(A, enc, N, s);
+        case 4: return states_dispatch<4>(A, enc, N, s);
+        case 5: return states_dispatch<5>(A, enc, N, s);
+        case 6: return states_dispatch<6>(A, enc, N, s);
+        case 7: return states_dispatch<7>(A, enc, N, s);
+        case 8: return states_dispatch<8>(A, enc, N, s);
+        case 9: return states_dispatch<9>(A, enc, N, s);
+        case 10: return states_dispatch<10>(A, enc, N, s);
+        default: set_error("BSC: unsupported Hprime %d", c->Hp); return PROSPER_EINVAL;
+    }
+}
+
+int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s) {
+    if (N <= 0) return PROSPER_OK;
+    const int H = c->H, D = c->D;
+    const size_t smem = sizeof(float) * ((size_t)H * AD + AT * AD + AT * PROSPER_MAX_HPRIME) +
+                        sizeof(int) * (AT * PROSPER_MAX_HPRIME + 3 * (H + 1));
+    static size_t attr_smem = 0;
+    if (smem > attr_smem) {
+        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_astat, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        attr_smem = smem;
+    }
+    const int slices = (D + AD - 1) / AD;
+    int ranges = std::max(1, c->num_sms / slices);
+    int64_t per = (N + ranges - 1) / ranges;
+    per = ((per + AT - 1) / AT) * AT;
+    ranges = (int)((N + per - 1) / per);
+    dim3 grid(slices, ranges);
+    k_astat<<<grid, 256, smem, s>>>(Y, c->sel, c->es, N, D, H, c->Hp, per, At);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+int launch_symmetrize(prosper_ctx *c, double *B, cudaStream_t s) {
+    const int H = c->H;
+    dim3 b(16, 16), g((H + 15) / 16, (H + 15) / 16);
+    k_symmetrize<<<g, b, 0, s>>>(B, H);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+}  // namespace prosper

@@ -1,0 +1,114 @@
+// internal.cuh -- shared declarations of libprosper's CUDA translation units.
+// Nothing here is part of the public C ABI (include/prosper.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/prosper.h"
+
+namespace prosper {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+
+#define PROSPER_CUDA_TRY(expr)                                                     \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            ::prosper::set_error("%s failed: %s (%s:%d)", #expr,                   \
+                                 cudaGetErrorString(_e), __FILE__, __LINE__);      \
+            return PROSPER_ECUDA;                                                  \
+        }                                                                          \
+    } while (0)
+
+#define PROSPER_LAUNCH_CHECK()                                                     \
+    do {                                                                           \
+        cudaError_t _e = cudaGetLastError();                                       \
+        if (_e != cudaSuccess) {                                                   \
+            ::prosper::set_error("kernel launch failed: %s (%s:%d)",               \
+                                 cudaGetErrorString(_e), __FILE__, __LINE__);      \
+            return PROSPER_ECUDA;                                                  \
+        }                                                                          \
+    } while (0)
+
+// Per-point scratch rows are padded to this many entries (Hprime <= 10).
+constexpr int SEL_STRIDE = 16;
+
+// Status word bits written by kernels (ctx->d_status).
+constexpr unsigned ST_NONFINITE = 1u;     // a data point had a non-finite y^T y
+constexpr unsigned ST_TC_TIMEOUT = 2u;    // a tensor-core pipeline wait gave up
+constexpr unsigned ST_CHOL_FAIL = 4u;     // M-step matrix not positive definite
+
+struct ServeState;  // serve.cu
+
+}  // namespace prosper
+
+struct prosper_ctx {
+    int model, D, H, Hp, gamma, precision;
+    int nK;                 // |K| = sum_{k<=gamma} C(Hp, k)
+    int64_t chunk;          // points per internal piece (scratch capacity)
+    int device, num_sms;
+
+    // per-iteration constants (rebuilt from W by every estep/encode call)
+    float *G = nullptr;       // H x H Gram matrix W^T W (FP32)
+    float *rnorm = nullptr;   // H: 1/||W_h|| (0 for a zero row)
+    float *Wd = nullptr;      // D x H: W in the paper's layout (FP32 SIMT projection operand)
+    uint16_t *Wb = nullptr;   // BF16 copy of W in the tcgen05 shared-memory image layout
+    float *mca_logW = nullptr;  // MCA: H x D log W_dh
+    float *gsc_tab = nullptr;   // GSC: per active subset {logdet, M_b^-1 packed} (8 floats)
+    int gsc_nsub = 0;
+
+    // per-piece scratch
+    int32_t *sel = nullptr;   // chunk x SEL_STRIDE selected latents (ascending)
+    float *selp = nullptr;    // chunk x SEL_STRIDE FP32 projections of the selected latents
+    float *yy = nullptr;      // chunk: y^T y
+    float *es = nullptr;      // chunk x SEL_STRIDE posterior means <s> of the selected latents
+
+    // M-step workspace (FP64)
+    double *mB = nullptr;     // H x H
+    double *mX = nullptr;     // H x D
+    double *msc = nullptr;    // 16 scalars
+
+    unsigned *d_status = nullptr;  // device status word (ST_* bits)
+
+    // host-staging for prosper_estep_host
+    float *h_stage = nullptr;
+    float *d_stage = nullptr;
+    int64_t stage_points = 0;
+
+    prosper::ServeState *serve = nullptr;
+};
+
+namespace prosper {
+
+// ------------------------------------------------------------ launchers
+// All launchers return PROSPER_OK or PROSPER_ECUDA (with set_error).
+int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s);
+int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s);
+int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t N,
+                         cudaStream_t s);
+int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_offset,
+                      prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
+                      float *mapp_out, float *logz_out, cudaStream_t s);
+int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s);
+int launch_symmetrize(prosper_ctx *c, double *B, cudaStream_t s);
+
+int launch_mca_prep(prosper_ctx *c, const float *W, cudaStream_t s);
+int launch_mca_estep(prosper_ctx *c, const float *W, const double *theta, const float *Y,
+                     int64_t N, prosper_stats *st, int16_t *sel_out, float *smean_out,
+                     int16_t *map_out, float *mapp_out, float *logz_out, cudaStream_t s);
+
+int launch_gsc_prep(prosper_ctx *c, const prosper_params *p, cudaStream_t s);
+int launch_gsc_estep(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
+                     prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
+                     float *mapp_out, float *logz_out, cudaStream_t s);
+
+int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_params *p,
+                 cudaStream_t s);
+
+// number of BSC projection-kernel tiles per persistent CTA etc. live in the .cu files
+
+}  // namespace prosper

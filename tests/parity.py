@@ -1,0 +1,52 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI,
+run the oracle on the same inputs, and compare with the stated tolerances.
+
+Tolerances (written here, used by every parity test):
+  - aggregated statistics At, B and the M-step's W: relative Frobenius error
+    <= 1e-5 (FP32 form);
+  - per-point posterior means <s> and q(MAP): max abs error <= 1e-5;
+  - F / N (truncated log-likelihood per point): relative error <= 1e-6;
+  - selections: identical except at score near-ties, where the GPU's set must
+    be optimal within tau = 1e-5 max|score| (FP32 form) or within the BF16
+    rounding bound (BF16 form); the oracle then re-runs with the GPU's set.
+"""
+import numpy as np
+
+REL_AGG = 1e-5
+ABS_POINT = 1e-5
+REL_F = 1e-6
+
+
+def relfro(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def check_selection(orc, model, Y, Wt, sel_gpu, Hp, tau_fn, mu=None, psi=None, pi=0.5, sigma=1.0):
+    """Return (n_differ, ok): every GPU set must be within tau of optimal."""
+    Yd = np.asarray(Y, np.float64)
+    orc_sel = None
+    n_diff = 0
+    bad = []
+    for n in range(len(Yd)):
+        sg = np.sort(np.asarray(sel_gpu[n][:Hp], np.int64))
+        sc = orc.scores(model, Yd[n], Wt, pi, sigma, mu=mu, psi=psi)
+        order = np.lexsort((np.arange(len(sc)), -sc))
+        so = np.sort(order[:Hp])
+        if np.array_equal(sg, so):
+            continue
+        n_diff += 1
+        kth = sc[order[Hp - 1]]
+        tau = tau_fn(n, sc)
+        if np.any(sc[sg] < kth - tau) or len(set(sg.tolist())) != Hp:
+            bad.append(n)
+    return n_diff, bad
+
+
+def torch_stats_to_numpy(st):
+    out = {}
+    for k, v in st.items():
+        out[k] = None if v is None else v.detach().cpu().numpy()
+    return out

@@ -1,0 +1,183 @@
+"""GPU parity of the BSC truncated E-step, encode and M-step (CUDA path through
+the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Model: Table 1 row BSC (linear superposition, Gaussian noise, binary latents,
+Bernoulli prior), Eq. 1-2; truncated posteriors and EM (Sec. 2); Hprime/gamma
+and step / inference (Sec. 3).
+"""
+import numpy as np
+import pytest
+
+from paper_1908_06843_gb300 import synth
+from parity import ABS_POINT, REL_AGG, REL_F, check_selection, relfro, torch_stats_to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _setup(ctxargs, Y, Wt, pi, sigma):
+    from paper_1908_06843_gb300 import Context
+    ctx = Context(*ctxargs)
+    dev = torch.device("cuda")
+    W = torch.tensor(np.asarray(Wt, np.float32), device=dev)
+    theta = torch.tensor([pi, sigma, 0.0, 0.0], dtype=torch.float64, device=dev)
+    Yg = torch.tensor(np.asarray(Y, np.float32), device=dev)
+    P = ctx.params(W, theta)
+    return ctx, W, theta, Yg, P
+
+
+def _fp32_tau(Y, Wt):
+    def tau(n, sc):
+        return 1e-5 * np.max(np.abs(sc)) + 1e-6
+    return tau
+
+
+def run_parity(orc, Y, Wt, pi, sigma, Hp, gamma, precision=0, tau_fn=None):
+    """E-step + encode on the GPU; oracle with the GPU's selection; compare."""
+    H, D = Wt.shape
+    Y32 = np.asarray(Y, np.float32)
+    Wt32 = np.asarray(Wt, np.float32).astype(np.float64)
+    ctx, W, theta, Yg, P = _setup((0, D, H, Hp, gamma, precision), Y32, Wt32, pi, sigma)
+    st = ctx.alloc_stats()
+    ctx.estep(P, Yg, st)
+    enc = ctx.encode(P, Yg)
+    torch.cuda.synchronize()
+    st = torch_stats_to_numpy(st)
+    enc = {k: v.cpu().numpy() for k, v in enc.items()}
+    sel = enc["sel"].astype(np.int32)
+    tau_fn = tau_fn or _fp32_tau(Y32, Wt32)
+    n_diff, bad = check_selection(orc, orc.BSC, Y32, Wt32, sel, Hp, tau_fn)
+    assert not bad, f"{len(bad)} selections not optimal within tau, e.g. point {bad[:5]}"
+    ref = orc.estep(orc.BSC, Y32, Wt32, pi, sigma, Hp, gamma, sel_in=sel)
+    assert relfro(st["At"], ref["At"]) <= REL_AGG, relfro(st["At"], ref["At"])
+    assert relfro(st["B"], ref["B"]) <= REL_AGG, relfro(st["B"], ref["B"])
+    N = len(Y32)
+    assert st["scal"][orc.SC_N] == N
+    assert abs(st["scal"][orc.SC_F] - ref["scal"][orc.SC_F]) <= REL_F * abs(ref["scal"][orc.SC_F])
+    assert abs(st["scal"][orc.SC_S1] - ref["scal"][orc.SC_S1]) <= REL_AGG * max(1.0, ref["scal"][orc.SC_S1])
+    assert abs(st["scal"][orc.SC_YY] - ref["scal"][orc.SC_YY]) <= 1e-6 * ref["scal"][orc.SC_YY]
+    # per point (encode)
+    assert np.max(np.abs(enc["s_mean"] - ref["smean"])) <= ABS_POINT
+    assert np.max(np.abs(enc["map_p"] - ref["map_p"])) <= ABS_POINT
+    np.testing.assert_allclose(enc["logZ"], ref["logZ"], rtol=1e-6, atol=2e-4)
+    mism = np.flatnonzero(np.any(enc["map_idx"] != ref["map_idx"], axis=1)) if gamma > 0 else []
+    for n in mism:   # MAP may differ only at exact-or-near ties of the log-joint
+        post = orc.posterior(orc.BSC, Y32[n], Wt32, pi, sigma, Hp, gamma, sel_in=sel[n])
+        qs = np.sort(post["q"])[::-1]
+        assert qs[0] - qs[1] <= 1e-5, (n, qs[:2])
+    return ctx, st, ref, n_diff, (W, theta, P)
+
+
+def test_bars_et_and_exact(orc):
+    """Bars workload (D=25, H=10, N=1000: ragged tail of the 64-point tiles):
+    ET H'=6, gamma=3 and exact EM H'=H=gamma=10."""
+    d = synth.bars(N=1000, seed=1001)
+    p = synth.init_bsc(d["Y"], 10, seed=2001, pi=0.5, normalise=False)
+    run_parity(orc, d["Y"], p["Wt"], p["pi"], p["sigma"], 6, 3)
+    run_parity(orc, d["Y"], d["Wt"], 0.2, 1.0, 6, 3)
+    run_parity(orc, d["Y"], d["Wt"], 0.2, 1.0, 10, 10)
+
+
+def test_gabor_shape_small_n(orc):
+    """D=256, H=256, H'=10, gamma=5 (638 states) on 2,050 points: 33 tiles, ragged tail."""
+    d = synth.gabor(N=2050, seed=1002)
+    p = synth.init_bsc(d["Y"], 256, seed=2002, pi=0.02, normalise=True)
+    run_parity(orc, d["Y"], d["Wt"], 4 / 256, 0.2, 10, 5)
+    run_parity(orc, d["Y"], p["Wt"], p["pi"], p["sigma"], 10, 5)
+
+
+@pytest.mark.parametrize("N", [1, 63, 64, 65, 257])
+def test_tile_edges(orc, N):
+    d = synth.gabor(N=N, seed=77, H=64)
+    run_parity(orc, d["Y"], d["Wt"], 0.05, 0.3, 7, 3)
+
+
+@pytest.mark.parametrize("Hp,gamma", [(1, 0), (1, 1), (4, 0), (5, 2), (8, 8), (9, 4)])
+def test_degenerate_state_sets(orc, Hp, gamma):
+    """gamma = 0 (only the empty state), H' = 1, H' = gamma (all 2^H' states)."""
+    d = synth.bars(N=300, seed=5, side=5)
+    run_parity(orc, d["Y"], d["Wt"], 0.2, 1.0, Hp, gamma)
+
+
+def test_empty_input_gives_zero_statistics(orc):
+    from paper_1908_06843_gb300 import Context
+    ctx = Context(0, 25, 10, 6, 3)
+    W = torch.randn(10, 25, device="cuda")
+    theta = torch.tensor([0.2, 1.0, 0, 0], dtype=torch.float64, device="cuda")
+    P = ctx.params(W, theta)
+    st = ctx.alloc_stats()
+    st["B"].fill_(7.0)
+    ctx.estep(P, torch.empty(0, 25, device="cuda"), st)
+    torch.cuda.synchronize()
+    assert float(st["B"].abs().sum()) == 0.0 and float(st["scal"].abs().sum()) == 0.0
+
+
+def test_mstep_matches_oracle(orc):
+    """FP64 M-step on the GPU's own statistics equals the oracle's M-step."""
+    d = synth.bars(N=1000, seed=1001)
+    p = synth.init_bsc(d["Y"], 10, seed=2001, pi=0.5, normalise=False)
+    ctx, st, ref, _, (W, theta, P) = run_parity(orc, d["Y"], p["Wt"], p["pi"], p["sigma"], 6, 3)
+    Wt0 = W.cpu().numpy().astype(np.float64)
+    W2, pi2, s2, _, _ = orc.mstep(orc.BSC, 1000, st, Wt0, p["pi"], p["sigma"])
+    stg = {k: (None if v is None else torch.tensor(v, device="cuda")) for k, v in st.items()}
+    ctx.mstep(stg, 1000, P)
+    torch.cuda.synchronize()
+    assert relfro(W.cpu().numpy(), W2) <= 1e-6
+    th = theta.cpu().numpy()
+    assert abs(th[0] - pi2) <= 1e-9 and abs(th[1] - s2) <= 1e-7 * s2
+
+
+def test_em_trajectory_on_bars(orc):
+    """20 EM iterations on the GPU; each step checked one at a time against the
+    oracle fed the GPU's parameters; the bars are recovered."""
+    from paper_1908_06843_gb300 import Context
+    d = synth.bars(N=1000, seed=1001)
+    p = synth.init_bsc(d["Y"], 10, seed=2001, pi=0.5, normalise=False)
+    ctx, W, theta, Yg, P = _setup((0, 25, 10, 6, 3, 0), d["Y"], p["Wt"], p["pi"], p["sigma"])
+    st = ctx.alloc_stats()
+    for it in range(50):
+        Wt_before = W.cpu().numpy().astype(np.float64)
+        th_before = theta.cpu().numpy().copy()
+        ctx.estep(P, Yg, st)
+        ctx.mstep(st, 1000, P)
+        torch.cuda.synchronize()
+        if it % 10 == 0:
+            ref = orc.estep(orc.BSC, d["Y"], Wt_before, th_before[0], th_before[1], 6, 3)
+            W2, _, _, _, _ = orc.mstep(orc.BSC, 1000, ref, Wt_before, th_before[0], th_before[1])
+            # near-tie selections can differ; compare the update loosely here, tightly above
+            assert relfro(W.cpu().numpy(), W2) <= 1e-3
+    Wl = W.cpu().numpy()
+    a = Wl - Wl.mean(1, keepdims=True)
+    b = d["Wt"] - d["Wt"].mean(1, keepdims=True)
+    C = (b / np.linalg.norm(b, axis=1, keepdims=True)) @ (a / np.linalg.norm(a, axis=1, keepdims=True)).T
+    from scipy.optimize import linear_sum_assignment
+    r, c = linear_sum_assignment(-C)
+    assert np.all(C[r, c] > 0.95)
+
+
+def test_full_size_sampled(orc):
+    """N = 200,000 Gabor points (the benchmark configuration): aggregate
+    invariants at full size and 256 sampled points against the oracle."""
+    d = synth.gabor(N=200_000, seed=1002)
+    Wt = d["Wt"].astype(np.float32).astype(np.float64)
+    ctx, W, theta, Yg, P = _setup((0, 256, 256, 10, 5, 0), d["Y"], Wt, 4 / 256, 0.2)
+    st = ctx.alloc_stats()
+    ctx.estep(P, Yg, st)
+    enc = ctx.encode(P, Yg)
+    torch.cuda.synchronize()
+    s = torch_stats_to_numpy(st)
+    assert s["scal"][3] == 200_000
+    np.testing.assert_allclose(s["B"], s["B"].T, atol=0)
+    # binary latents: B_hh = sum_n <s_h>_n, sum_h B_hh = sum <|s|>
+    assert abs(np.trace(s["B"]) - s["scal"][1]) <= 1e-9 * s["scal"][1]
+    F_enc = float(enc["logZ"].double().sum())
+    assert abs(F_enc - s["scal"][0]) <= 1e-6 * abs(s["scal"][0])
+    g = synth.rng(3)
+    idx = np.sort(g.choice(200_000, 256, replace=False))
+    sel = enc["sel"].cpu().numpy()[idx].astype(np.int32)
+    Ys = d["Y"][idx]
+    n_diff, bad = check_selection(orc, orc.BSC, Ys, Wt, sel, 10, _fp32_tau(Ys, Wt))
+    assert not bad
+    ref = orc.estep(orc.BSC, Ys, Wt, 4 / 256, 0.2, 10, 5, sel_in=sel)
+    assert np.max(np.abs(enc["s_mean"].cpu().numpy()[idx] - ref["smean"])) <= ABS_POINT
+    assert np.max(np.abs(enc["map_p"].cpu().numpy()[idx] - ref["map_p"])) <= ABS_POINT
