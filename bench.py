@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the ProSper truncated E-step on GB300.
+
+Workload: BSC on image-patch-shaped synthetic data -- D = 16x16 = 256,
+H = 256 random unit-norm Gabor filters, s_h ~ Bernoulli(4/256),
+y = W s + N(0, 0.2^2), N = 200,000 points per GPU (Y = 204.8 MB FP32, larger
+than the 129 MB L2, so no flush is needed between steps); ET with H' = 10,
+gamma = 5 (638 states per point); Theta = the generating W, pi = 4/256,
+sigma = 0.2.
+
+One step = one truncated E-step over the N points: per-iteration constants
+(Gram matrix, norms, dictionary copies), projection + top-H' preselection,
+the state evaluation / log-sum-exp / posterior moments, and the sufficient
+statistics sum y<s>^T, sum <ss^T>, F, sum<|s|>, sum y^T y.  The headline value
+is the BF16-projection + FP32-rescore form; the plain FP32 form is reported
+beside it ("forms").  The FP64 M-step and the encode path are timed as extra
+keys.  Multi-GPU (torchrun) is weak scaling: every rank runs its own
+200,000-point shard; no collective is on the data path (the statistics
+all-reduce belongs to the M-step side and is not part of the E-step metric).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on bounded
+samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "E-step data points/sec (BSC H=256,H'=10,gamma=5) BF16 vs FP32 at stated error; serve p50/p99"
+D, H, HP, GAMMA, NPTS = 256, 256, 10, 5, 200_000
+PI, SIGMA = 4.0 / 256.0, 0.2
+WORKLOAD = "BSC Gabor patches D=256 H=256 H'=10 gamma=5 (638 states) N=200000/GPU"
+
+# FP32 lane throughput of GB300: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock);
+# one FMA or add counts as one lane operation.
+SMS, LANES, FMAX_GHZ = 152, 128, 2.07
+ALU_PEAK_TOPS = SMS * LANES * FMAX_GHZ * 1e9 / 1e12   # 40.28 T lane-ops/s
+
+# Algorithmic work per data point of each kernel ("Kernels").
+KERNEL_WORK = {
+    # kernel: (bound, units per point, unit)
+    "bsc_proj_f32": ("alu", D * H, "lane-op"),            # W^T y: D*H FMA
+    "bsc_proj_bf16": ("hbm", 4 * D, "byte"),              # Y read once (FP32)
+    "bsc_states": ("alu", 3198 + 1276 + 2560 + 6745, "lane-op"),
+    "astat": ("hbm", 4 * D + 8 * 16, "byte"),             # Y re-read + per-point records
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j.get("hbm_gbs", 6800.0)), float(j.get("bf16_tflops", 1900.0)), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_data(rank):
+    from paper_1908_06843_gb300 import synth
+    d = synth.gabor(N=NPTS, seed=1002 + 1000 * rank)
+    return d["Y"], d["Wt"].astype(np.float32)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(Y, Wt, target_s):
+    """FP64 oracle E-step on a bounded sample sized for about target_s seconds."""
+    import oracle
+    oracle.build()
+    Wd = Wt.astype(np.float64)
+    n = 64
+    t0 = time.perf_counter()
+    oracle.estep(oracle.BSC, Y[:n], Wd, PI, SIGMA, HP, GAMMA)
+    dt = time.perf_counter() - t0
+    n2 = int(min(len(Y), max(n, n * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.estep(oracle.BSC, Y[:n2], Wd, PI, SIGMA, HP, GAMMA)
+    dt2 = time.perf_counter() - t0
+    return n2, dt2
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    Y, Wt = make_data(0)
+    import oracle
+    oracle.build()
+    # size one step for ~4 s of host work so warm-up + steps stay within minutes
+    n_step, dt = time_oracle(Y, Wt, 1.0)
+    n_step = max(16, int(n_step * 4.0 / max(dt, 1e-3)))
+    n_step = min(n_step, len(Y))
+    Wd = Wt.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.estep(oracle.BSC, Y[:n_step], Wd, PI, SIGMA, HP, GAMMA)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        a = (k * n_step) % max(1, len(Y) - n_step)
+        oracle.estep(oracle.BSC, Y[a:a + n_step], Wd, PI, SIGMA, HP, GAMMA)
+    el = time.perf_counter() - t0
+    value = n_step * args.steps / el
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (Y 204.8 MB)"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cpu_cores(),
+                         "kind": "oracle",
+                         "sample": f"{n_step} of the {NPTS} points per step (FP64 C oracle, OpenMP)"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def bench_form(torch, ctx, P, Yg, st, steps, warmup, dist, sampler):
+    for _ in range(warmup):
+        ctx.estep(P, Yg, st)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.estep(P, Yg, st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    # traced pass of the same steps: per-kernel device time with CUDA events
+    ctx.trace_enable(True)
+    for _ in range(steps):
+        ctx.estep(P, Yg, st)
+    kern = ctx.trace_read()
+    ctx.trace_enable(False)
+    return ms, kern, clocks
+
+
+def roofline(kern, steps, hbm_peak, peak_kind, npts):
+    per = {k: v[0] / steps for k, v in kern.items()}
+    total = sum(per.values())
+    top = max((k for k in per if k in KERNEL_WORK), key=lambda k: per[k])
+    bound, units, unit = KERNEL_WORK[top]
+    launches = kern[top][1] / steps
+    sec = per[top] / launches * 1e-3
+    if bound == "alu":
+        achieved = units * npts / sec / 1e12
+        rl = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS,
+              "unit": "Tlane-op/s", "frac": achieved / ALU_PEAK_TOPS,
+              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
+    else:
+        achieved = units * npts / sec / 1e9
+        rl = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+              "frac": achieved / hbm_peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    rl["kernel"] = top
+    rl["traffic"] = None
+    shares = {k: {"ms_per_step": v, "share": v / total,
+                  "launches_per_step": kern[k][1] / steps} for k, v in per.items()}
+    return rl, shares
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1908_06843_gb300 import BF16_RESCORE, FP32, Context
+
+    ws, rank, local = dist_info()
+    dist = None
+    if ws > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Y, Wt = make_data(rank)
+    Yg = torch.tensor(Y, device=dev)
+    hbm_peak, bf16_peak, peak_kind = load_peaks()
+
+    forms = {}
+    for name, prec in [("bf16_rescore", BF16_RESCORE), ("fp32", FP32)]:
+        try:
+            ctx = Context(0, D, H, HP, GAMMA, prec)
+        except Exception as e:    # a form that cannot be built is reported, not faked
+            forms[name] = {"error": str(e)}
+            continue
+        W = torch.tensor(Wt, device=dev)
+        theta = torch.tensor([PI, SIGMA, 0.0, 0.0], dtype=torch.float64, device=dev)
+        P = ctx.params(W, theta)
+        st = ctx.alloc_stats()
+        sampler = ClockSampler(local) if rank == 0 else None
+        ms, kern, clocks = bench_form(torch, ctx, P, Yg, st, args.steps, args.warmup, dist, sampler)
+        rl, shares = roofline(kern, args.steps, hbm_peak, peak_kind, NPTS)
+        launches = sum(v[1] for v in kern.values()) / args.steps
+        # M-step and encode (timed separately; not part of the E-step metric)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Wsave = W.clone()
+        thsave = theta.clone()
+        e0.record()
+        for _ in range(3):
+            ctx.mstep(st, NPTS, P)
+            W.copy_(Wsave)
+            theta.copy_(thsave)
+        e1.record()
+        torch.cuda.synchronize()
+        mstep_ms = e0.elapsed_time(e1) / 3
+        enc = ctx.encode(P, Yg)
+        e0.record()
+        for _ in range(5):
+            ctx.encode(P, Yg, out=enc)
+        e1.record()
+        torch.cuda.synchronize()
+        encode_ms = e0.elapsed_time(e1) / 5
+        # end to end through the C ABI with host buffers (pinned), copies inside
+        Yh = torch.from_numpy(Y).pin_memory()
+        At_h = np.zeros((H, D))
+        B_h = np.zeros((H, H))
+        sc_h = np.zeros(8)
+        for _ in range(2):
+            ctx.estep_host(P, Yh, At_h, B_h, sc_h)
+        e2e_steps = max(3, min(args.steps, 20))
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.estep_host(P, Yh, At_h, B_h, sc_h)
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        forms[name] = {
+            "value": NPTS * ws * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "roofline": rl, "kernels": shares, "gpu_launches_per_step": launches,
+            "clocks": clocks, "mstep_ms": mstep_ms, "encode_ms": encode_ms,
+            "em_iteration_ms": ms / args.steps + mstep_ms,
+            "e2e": {"value": NPTS * ws * e2e_steps / e2e_s, "unit": "points/s",
+                    "h2d_bytes_per_step": NPTS * D * 4,
+                    "d2h_bytes_per_step": (H * D + H * H + 8) * 8},
+            "F_per_point": float(st["scal"][0].item()) / NPTS,
+        }
+        ctx.close()
+        del P, st
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    head_name = "bf16_rescore" if "value" in forms.get("bf16_rescore", {}) else "fp32"
+    head = forms[head_name]
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_s, dt = time_oracle(Y, Wt, args.cpu_seconds)
+        cpu = {"value": n_s / dt, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first {n_s} of the {NPTS} points, one FP64 oracle E-step ({dt:.1f} s)"}
+    out = {
+        "metric": METRIC, "value": head["value"], "unit": "points/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32" if head_name == "bf16_rescore" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": head_name, "global_points": NPTS * ws,
+                   "l2": "inputs larger than L2 (Y 204.8 MB per GPU), no flush",
+                   "parallelism": f"weak x{ws}, no data-path collective"},
+        "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"],
+        "clocks": head["clocks"], "gpu_launches": int(round(head["gpu_launches_per_step"] * args.steps)),
+        "forms": forms,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -148,6 +148,15 @@ int prosper_estep_host(prosper_ctx *ctx, const prosper_params *p, const float *Y
                        int64_t N, double *At_host, double *B_host, double *scal_host,
                        void *stream);
 
+/* Kernel tracing (measurement aid, not part of the method).  While enabled,
+ * every kernel the context launches is bracketed by CUDA events recorded on
+ * its stream.  prosper_trace_read synchronises the device, writes up to max
+ * distinct kernel names (each a NUL-terminated string in a 48-byte slot of
+ * names), their summed device time in ms and their launch counts, clears the
+ * record, and returns the number of distinct kernels (or a negative error). */
+int prosper_trace_enable(prosper_ctx *ctx, int on);
+int prosper_trace_read(prosper_ctx *ctx, int max, char *names, double *total_ms, int *launches);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *prosper_last_error(void);
 

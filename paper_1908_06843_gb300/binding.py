@@ -39,6 +39,8 @@ ABI = {
     "prosper_serve_wait": (_I, [_P, ctypes.c_uint64, _I, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "prosper_serve_stop": (_I, [_P]),
+    "prosper_trace_enable": (_I, [_P, _I]),
+    "prosper_trace_read": (_I, [_P, _I, _P, _P, _P]),
 }
 
 
@@ -194,6 +196,22 @@ class Context:
                                            _ptr(At_host), _ptr(B_host), _ptr(scal_host),
                                            _stream(stream)), "prosper_estep_host")
         return dict(At=At_host, B=B_host, scal=scal_host)
+
+    # ------------------------------------------------------------- tracing
+    def trace_enable(self, on=True):
+        _check(self.lib.prosper_trace_enable(self.h, 1 if on else 0), "prosper_trace_enable")
+
+    def trace_read(self, max_kernels=32):
+        """{kernel name: (total ms, launches)} since the last read (synchronises)."""
+        names = ctypes.create_string_buffer(48 * max_kernels)
+        ms = np.zeros(max_kernels)
+        cnt = np.zeros(max_kernels, np.int32)
+        k = self.lib.prosper_trace_read(self.h, max_kernels, names, _ptr(ms), _ptr(cnt))
+        if k < 0:
+            _check(k, "prosper_trace_read")
+        raw = names.raw
+        return {raw[48 * i:48 * i + 48].split(b"\0")[0].decode(): (float(ms[i]), int(cnt[i]))
+                for i in range(k)}
 
     # ------------------------------------------------------------- serving
     def serve_start(self, P: Params, n_slots=4, slot_points=8192):

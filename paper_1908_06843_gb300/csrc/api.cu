@@ -5,7 +5,10 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstring>
+#include <map>
 #include <new>
+#include <string>
+#include <vector>
 
 namespace prosper {
 
@@ -16,6 +19,29 @@ void set_error(const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+struct TraceRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+struct TraceState {
+    bool on = false;
+    std::vector<TraceRec> recs;
+};
+
+TraceScope::TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream)
+    : c(ctx), s(stream), on(ctx && ctx->trace && ctx->trace->on) {
+    if (!on) return;
+    TraceRec r{name, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, s);
+    c->trace->recs.push_back(r);
+}
+
+TraceScope::~TraceScope() {
+    if (on) cudaEventRecord(c->trace->recs.back().b, s);
 }
 
 static int num_states(int Hp, int gamma) {
@@ -187,9 +213,48 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     return PROSPER_OK;
 }
 
+int prosper_trace_enable(prosper_ctx *c, int on) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    if (!c->trace) c->trace = new TraceState();
+    c->trace->on = on != 0;
+    return PROSPER_OK;
+}
+
+int prosper_trace_read(prosper_ctx *c, int max, char *names, double *total_ms, int *launches) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    if (!c->trace) return 0;
+    PROSPER_CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<std::string> order;
+    std::map<std::string, std::pair<double, int>> acc;
+    for (auto &r : c->trace->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        auto it = acc.find(r.name);
+        if (it == acc.end()) { order.push_back(r.name); acc[r.name] = {ms, 1}; }
+        else { it->second.first += ms; it->second.second += 1; }
+    }
+    c->trace->recs.clear();
+    int k = 0;
+    for (auto &nm : order) {
+        if (k >= max) break;
+        if (names) { strncpy(names + 48 * k, nm.c_str(), 47); names[48 * k + 47] = 0; }
+        if (total_ms) total_ms[k] = acc[nm].first;
+        if (launches) launches[k] = acc[nm].second;
+        ++k;
+    }
+    return k;
+}
+
 int prosper_destroy(prosper_ctx *c) {
     if (!c) return PROSPER_OK;
     if (c->serve) prosper_serve_stop(c);
+    if (c->trace) {
+        for (auto &r : c->trace->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        delete c->trace;
+    }
+    cudaFree(c->d_hstats);
     cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
     cudaFree(c->mca_logW); cudaFree(c->gsc_tab);
     cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es);
@@ -272,16 +337,10 @@ int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_h
         PROSPER_CUDA_TRY(cudaMalloc(&c->d_stage, bytes));
         c->stage_points = piece;
     }
-    static thread_local double *d_stats = nullptr;
-    static thread_local size_t d_stats_len = 0;
     const size_t need = H * D + H * H + PROSPER_SC_LEN + 3 * H + 2 * H * D;
-    if (d_stats_len < need) {
-        if (d_stats) cudaFree(d_stats);
-        PROSPER_CUDA_TRY(cudaMalloc(&d_stats, sizeof(double) * need));
-        d_stats_len = need;
-    }
+    if (!c->d_hstats) PROSPER_CUDA_TRY(cudaMalloc(&c->d_hstats, sizeof(double) * need));
     prosper_stats st;
-    st.At = d_stats;
+    st.At = c->d_hstats;
     st.B = st.At + H * D;
     st.scal = st.B + H * H;
     st.gsc = st.scal + PROSPER_SC_LEN;

@@ -286,6 +286,7 @@ struct StateArgs {
     int16_t *sel_out, *map_out;
     float *smean_out, *mapp_out, *logz_out;
     int64_t n_offset;   // row offset of this piece in the encode outputs
+    prosper_ctx *trace_ctx;
 };
 
 // One thread per data point.  Local units 0..LB-1 ("lo") are enumerated by a
@@ -653,6 +654,7 @@ __global__ void k_symmetrize(double *B, int H) {
 // ================================================================ launchers
 int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
     const int H = c->H, D = c->D;
+    TraceScope tr(c, "bsc_prep", s);
     dim3 gb(16, 16), gg((H + 15) / 16, (H + 15) / 16);
     k_gram<<<gg, gb, 0, s>>>(W, H, D, c->G);
     PROSPER_LAUNCH_CHECK();
@@ -677,6 +679,7 @@ int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t 
     }
     int64_t ntiles = (N + PT - 1) / PT;
     int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
+    TraceScope tr(c, "bsc_proj_f32", s);
     k_bsc_proj_f32<<<grid, 256, smem, s>>>(Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->sel,
                                            c->selp, c->yy, c->d_status);
     PROSPER_LAUNCH_CHECK();
@@ -686,6 +689,7 @@ int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t 
 template <int HP>
 static int states_dispatch(StateArgs &A, bool encode, int64_t N, cudaStream_t s) {
     int grid = (int)((N + 255) / 256);
+    TraceScope tr(A.trace_ctx, encode ? "bsc_states_encode" : "bsc_states", s);
     if (encode) k_bsc_states<HP, true><<<grid, 256, 0, s>>>(A);
     else k_bsc_states<HP, false><<<grid, 256, 0, s>>>(A);
     PROSPER_LAUNCH_CHECK();
@@ -703,7 +707,7 @@ int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_
     A.B = st ? st->B : nullptr;
     A.scal = st ? st->scal : nullptr;
     A.sel_out = sel_out; A.map_out = map_out; A.smean_out = smean_out; A.mapp_out = mapp_out;
-    A.logz_out = logz_out; A.n_offset = n_offset;
+    A.logz_out = logz_out; A.n_offset = n_offset; A.trace_ctx = c;
     const bool enc = (st == nullptr);
     switch (c->Hp) {
         case 1: return states_dispatch<1>(A, enc, N, s);
@@ -737,6 +741,7 @@ int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStre
     per = ((per + AT - 1) / AT) * AT;
     ranges = (int)((N + per - 1) / per);
     dim3 grid(slices, ranges);
+    TraceScope tr(c, "astat", s);
     k_astat<<<grid, 256, smem, s>>>(Y, c->sel, c->es, N, D, H, c->Hp, per, At);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
@@ -745,6 +750,7 @@ int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStre
 int launch_symmetrize(prosper_ctx *c, double *B, cudaStream_t s) {
     const int H = c->H;
     dim3 b(16, 16), g((H + 15) / 16, (H + 15) / 16);
+    TraceScope tr(c, "symmetrize", s);
     k_symmetrize<<<g, b, 0, s>>>(B, H);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;

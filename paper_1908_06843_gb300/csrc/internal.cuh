@@ -43,6 +43,17 @@ constexpr unsigned ST_TC_TIMEOUT = 2u;    // a tensor-core pipeline wait gave up
 constexpr unsigned ST_CHOL_FAIL = 4u;     // M-step matrix not positive definite
 
 struct ServeState;  // serve.cu
+struct TraceState;  // api.cu
+
+// Kernel tracing (prosper_trace_enable): CUDA events recorded around every
+// kernel launch on the launching stream.  TraceScope is a no-op when off.
+struct TraceScope {
+    prosper_ctx *c;
+    cudaStream_t s;
+    bool on;
+    TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream);
+    ~TraceScope();
+};
 
 }  // namespace prosper
 
@@ -80,6 +91,8 @@ struct prosper_ctx {
     int64_t stage_points = 0;
 
     prosper::ServeState *serve = nullptr;
+    prosper::TraceState *trace = nullptr;
+    double *d_hstats = nullptr;   // device statistics of prosper_estep_host
 };
 
 namespace prosper {
