@@ -193,7 +193,7 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
         ALLOC(c->sel, ch * SEL_STRIDE);
         ALLOC(c->selp, ch * SEL_STRIDE);
         ALLOC(c->es, ch * SEL_STRIDE);
-        ALLOC(c->yy, ch);
+        ALLOC(c->yy, ch * 2);
     }
     if (model == PROSPER_MCA) ALLOC(c->mca_logW, (size_t)H * D);
     if (model == PROSPER_GSC) {

@@ -116,24 +116,63 @@ constexpr int PH = 256;       // max H of this kernel
 constexpr int PS = PH + 4;    // padded row of the projection tile in smem
 
 struct ProjSmem {
-    float Ys[PK][PT];         // 8 KB   (d-major so a thread reads 8 points with 2 LDS.128)
-    float Ws[PK][PH];         // 32 KB
+    float Ys[2][PK][PT];      // 16 KB  (d-major so a thread reads 8 points with 2 LDS.128)
+    float Ws[2][PK][PH];      // 64 KB
     float Ps[PT][PS];         // 66.5 KB
 };
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = pred ? 16 : 0;   // src-size 0 zero-fills the 16 bytes
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Error-free sum of squares of one point's row (double-float: hi + lo), one warp.
+__device__ __forceinline__ float2 warp_sumsq_df(const float *row, int D, int lane) {
+    float hi = 0.f, lo = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        const float v = row[d];
+        const float p = v * v;
+        const float pe = fmaf(v, v, -p);        // exact error of the product
+        const float s = hi + p;                 // TwoSum(hi, p)
+        const float bb = s - hi;
+        lo += ((hi - (s - bb)) + (p - bb)) + pe;
+        hi = s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = hi + h2;
+        const float bb = s - hi;
+        lo = lo + l2 + ((hi - (s - bb)) + (h2 - bb));
+        hi = s;
+    }
+    return make_float2(hi, lo);
+}
+
 // Grid: persistent, one 256-thread CTA per SM.  Thread (tp = tid & 7, th = tid >> 3)
-// accumulates the 8 x 8 block P[tp*8 + i][th*8 + j] of the 64 x 256 tile.
+// accumulates the 8 x 8 block P[tp*8 + i][th*8 + j] of the 64 x 256 tile.  The
+// k-chunks of all tiles form one software pipeline: while chunk q is multiplied,
+// the Y values of chunk q+1 are in flight into registers and its W rows into the
+// other shared-memory stage (cp.async).
 __global__ void __launch_bounds__(256, 1)
 k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
                const float *__restrict__ rnorm, int64_t N, int D, int H, int Hp,
                int32_t *__restrict__ sel_out, float *__restrict__ selp_out,
-               float *__restrict__ yy_out, unsigned *__restrict__ status) {
+               float2 *__restrict__ yy_out, unsigned *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ProjSmem &sm = *reinterpret_cast<ProjSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tp = tid & 7, th = tid >> 3;
     const int64_t ntiles = (N + PT - 1) / PT;
-    const bool vecY = (D % 4) == 0, vecW = (H % 4) == 0;
+    const bool vecY = (D % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+    const bool vecW = (H % 4) == 0;
+    const int nk = (D + PK - 1) / PK;
+    const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const int64_t nq = my_tiles * nk;   // chunks this CTA processes
 
     float rn[8];
 #pragma unroll
@@ -142,80 +181,110 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
         rn[j] = h < H ? rnorm[h] : 0.f;
     }
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t n0 = tile * PT;
-        float acc[8][8];
+    // Y chunk mapping: thread loads float4 (q4 = idx & 7) of point p = idx >> 3, idx = tid + 256 r
+    float4 yreg[2];
+    auto load_y = [&](int64_t q) {
+        const int64_t tile = blockIdx.x + (q / nk) * gridDim.x;
+        const int k0 = (int)(q % nk) * PK;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-
-        for (int k0 = 0; k0 < D; k0 += PK) {
-            // Y chunk: 64 points x 32 d, stored transposed
-            for (int idx = tid; idx < PT * (PK / 4); idx += 256) {
-                int p = idx >> 3, q = idx & 7;
-                int64_t n = n0 + p;
-                int d = k0 + q * 4;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (n < N) {
-                    const float *row = Y + n * D;
-                    if (vecY && d + 3 < D) {
-                        v = __ldg(reinterpret_cast<const float4 *>(row + d));
-                    } else {
-                        if (d < D) v.x = row[d];
-                        if (d + 1 < D) v.y = row[d + 1];
-                        if (d + 2 < D) v.z = row[d + 2];
-                        if (d + 3 < D) v.w = row[d + 3];
-                    }
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + 256 * r;
+            const int p = idx >> 3, q4 = idx & 7;
+            const int64_t n = tile * PT + p;
+            const int d = k0 + q4 * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (n < N) {
+                const float *row = Y + n * D;
+                if (vecY && d + 3 < D) {
+                    v = __ldg(reinterpret_cast<const float4 *>(row + d));
+                } else {
+                    if (d < D) v.x = row[d];
+                    if (d + 1 < D) v.y = row[d + 1];
+                    if (d + 2 < D) v.z = row[d + 2];
+                    if (d + 3 < D) v.w = row[d + 3];
                 }
-                sm.Ys[q * 4 + 0][p] = v.x;
-                sm.Ys[q * 4 + 1][p] = v.y;
-                sm.Ys[q * 4 + 2][p] = v.z;
-                sm.Ys[q * 4 + 3][p] = v.w;
             }
-            // W chunk: 32 d x 256 h
-            for (int idx = tid; idx < PK * (PH / 4); idx += 256) {
-                int kk = idx >> 6, c4 = (idx & 63) * 4;
-                int d = k0 + kk;
+            yreg[r] = v;
+        }
+    };
+    auto store_y = [&](int st) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + 256 * r;
+            const int p = idx >> 3, q4 = idx & 7;
+            sm.Ys[st][q4 * 4 + 0][p] = yreg[r].x;
+            sm.Ys[st][q4 * 4 + 1][p] = yreg[r].y;
+            sm.Ys[st][q4 * 4 + 2][p] = yreg[r].z;
+            sm.Ys[st][q4 * 4 + 3][p] = yreg[r].w;
+        }
+    };
+    auto load_w = [&](int64_t q, int st) {
+        const int k0 = (int)(q % nk) * PK;
+        for (int idx = tid; idx < PK * (PH / 4); idx += 256) {
+            const int kk = idx >> 6, c4 = (idx & 63) * 4;
+            const int d = k0 + kk;
+            const float *src = Wd + (size_t)(d < D ? d : 0) * H + c4;
+            if (vecW) {
+                cp_async16(&sm.Ws[st][kk][c4], src, d < D && c4 < H);
+            } else {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (d < D) {
-                    const float *row = Wd + (size_t)d * H;
-                    if (vecW && c4 + 3 < H) {
-                        v = __ldg(reinterpret_cast<const float4 *>(row + c4));
-                    } else {
-                        if (c4 < H) v.x = row[c4];
-                        if (c4 + 1 < H) v.y = row[c4 + 1];
-                        if (c4 + 2 < H) v.z = row[c4 + 2];
-                        if (c4 + 3 < H) v.w = row[c4 + 3];
-                    }
+                    if (c4 < H) v.x = src[0];
+                    if (c4 + 1 < H) v.y = src[1];
+                    if (c4 + 2 < H) v.z = src[2];
+                    if (c4 + 3 < H) v.w = src[3];
                 }
-                *reinterpret_cast<float4 *>(&sm.Ws[kk][c4]) = v;
+                *reinterpret_cast<float4 *>(&sm.Ws[st][kk][c4]) = v;
             }
-            __syncthreads();
-#pragma unroll 4
-            for (int kk = 0; kk < PK; ++kk) {
-                float4 y0 = *reinterpret_cast<const float4 *>(&sm.Ys[kk][tp * 8]);
-                float4 y1 = *reinterpret_cast<const float4 *>(&sm.Ys[kk][tp * 8 + 4]);
-                float4 w0 = *reinterpret_cast<const float4 *>(&sm.Ws[kk][th * 8]);
-                float4 w1 = *reinterpret_cast<const float4 *>(&sm.Ws[kk][th * 8 + 4]);
-                float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-                float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(yv[i], wv[j], acc[i][j]);
-            }
-            __syncthreads();
         }
+        cp_async_commit();
+    };
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    if (nq > 0) {
+        load_y(0);
+        load_w(0, 0);
+    }
+    for (int64_t q = 0; q < nq; ++q) {
+        const int st = (int)(q & 1);
+        store_y(st);
+        cp_async_wait_all();
+        __syncthreads();
+        if (q + 1 < nq) {
+            load_y(q + 1);
+            load_w(q + 1, st ^ 1);
+        }
+#pragma unroll 4
+        for (int kk = 0; kk < PK; ++kk) {
+            float4 y0 = *reinterpret_cast<const float4 *>(&sm.Ys[st][kk][tp * 8]);
+            float4 y1 = *reinterpret_cast<const float4 *>(&sm.Ys[st][kk][tp * 8 + 4]);
+            float4 w0 = *reinterpret_cast<const float4 *>(&sm.Ws[st][kk][th * 8]);
+            float4 w1 = *reinterpret_cast<const float4 *>(&sm.Ws[st][kk][th * 8 + 4]);
+            float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+            float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(yv[i], wv[j], acc[i][j]);
+        }
+        if ((q % nk) != nk - 1) continue;
+
+        // ---- tile epilogue: projections to shared memory, then preselection
+        const int64_t n0 = (blockIdx.x + (q / nk) * gridDim.x) * PT;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float *row = &sm.Ps[tp * 8 + i][th * 8];
             *reinterpret_cast<float4 *>(row) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
             *reinterpret_cast<float4 *>(row + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
         }
         __syncthreads();
-
-        // selection: warp w takes points w*8 .. w*8+7 of the tile
         for (int i = 0; i < PT / 8; ++i) {
             const int p = warp * (PT / 8) + i;
             const int64_t n = n0 + p;
@@ -228,7 +297,6 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
             }
             int sel[PROSPER_MAX_HPRIME];
             warp_topk<PROSPER_MAX_HPRIME>(key, Hp, sel, lane);
-            // lane r < Hp writes its round's latent at its ascending rank
             int myh = 0x7fffffff;
 #pragma unroll
             for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
@@ -240,18 +308,10 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
                 sel_out[n * SEL_STRIDE + rank] = myh;
                 selp_out[n * SEL_STRIDE + rank] = sm.Ps[p][myh];
             }
-            // y^T y of the point (also the non-finite-input check)
-            float s = 0.f;
-            const float *row = Y + n * D;
-            for (int d = lane; d < D; d += 32) {
-                float v = row[d];
-                s = fmaf(v, v, s);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const float2 yy = warp_sumsq_df(Y + n * D, D, lane);
             if (lane == 0) {
-                yy_out[n] = s;
-                if (!isfinite(s)) atomicOr(status, ST_NONFINITE);
+                yy_out[n] = yy;
+                if (!isfinite(yy.x)) atomicOr(status, ST_NONFINITE);
             }
         }
         __syncthreads();
@@ -261,20 +321,22 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
 // ----------------------------------------------------------- state kernel
 __host__ __device__ constexpr int cpopc(int x) { return x == 0 ? 0 : (x & 1) + cpopc(x >> 1); }
 __host__ __device__ constexpr int cctz(int x) { return (x & 1) ? 0 : 1 + cctz(x >> 1); }
+// sum over the hi units u in t of 2^(HP-1-(LB+u)): the weight of t in the
+// bit-reversed state mask (lower local unit = higher weight).
+__host__ __device__ constexpr int crev_hi(int t, int LB, int HP) {
+    return t == 0 ? 0 : ((t & 1) << (HP - 1 - LB)) + crev_hi(t >> 1, LB + 1, HP);
+}
 
-// canonical order of states: fewer active units first, then lexicographic
-// order of the sorted local-index lists (lowest differing unit decides).
-__device__ __forceinline__ bool canon_less(unsigned a, unsigned b) {
-    int pa = __popc(a), pb = __popc(b);
-    if (pa != pb) return pa < pb;
-    unsigned d = a ^ b;
-    return d != 0u && (a & (d & (0u - d))) != 0u;
+__device__ __forceinline__ float fast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 struct StateArgs {
     const int32_t *sel;
     const float *selp;
-    const float *yy;
+    const float2 *yy;
     const float *G;
     int64_t N;
     int H, D, gamma;
@@ -289,20 +351,47 @@ struct StateArgs {
     prosper_ctx *trace_ctx;
 };
 
+// L(lo) = sum_{j in lo} a_j + sum_{i<j in lo} b_ij and c_u(lo) = a_u + sum_{i in lo} b_iu,
+// evaluated branch-free with 0/1 multipliers (fmaf(0, x, s) = s and
+// fmaf(1, x, s) = s + x exactly, so this equals the plain sums).
+template <int HP, int LB, int HB>
+__device__ __forceinline__ void lo_terms(int lo, const float (&a)[HP], const float (&b)[HP][HP],
+                                         float (&mk)[LB > 0 ? LB : 1], float &L, float (&c)[HB]) {
+#pragma unroll
+    for (int i = 0; i < LB; ++i) mk[i] = (float)((lo >> i) & 1);
+    L = 0.f;
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+        L = fmaf(mk[i], a[i], L);
+#pragma unroll
+        for (int j = i + 1; j < LB; ++j) L = fmaf(mk[i] * mk[j], b[i][j], L);
+    }
+#pragma unroll
+    for (int u = 0; u < HB; ++u) {
+        float v = a[LB + u];
+#pragma unroll
+        for (int i = 0; i < LB; ++i) v = fmaf(mk[i], b[i][LB + u], v);
+        c[u] = v;
+    }
+}
+
 // One thread per data point.  Local units 0..LB-1 ("lo") are enumerated by a
 // warp-uniform loop; units LB..HP-1 ("hi", HB = min(HP,5) of them) are
 // unrolled, so each lo pattern evaluates its 2^HB hi patterns from registers:
-//   l(lo, t) = L(lo) + sum_{u in t} c_u(lo) + M(t),
-//   L(lo)  = sum_{j in lo} a_j + sum_{i<j in lo} b_ij,
-//   c_u(lo) = a_u + sum_{i in lo} b_iu,   M(t) = sum_{u<v in t} b_uv,
+//   l(lo, t) = L(lo) + sum_{u in t} c_u(lo) + M(t),   M(t) = sum_{u<v in t} b_uv,
 // with a_j = log2e (log(pi/(1-pi)) + (p_j - G_jj/2)/sigma^2), b_ij = -log2e G_ij/sigma^2.
-// States with more than gamma active units are skipped by warp-uniform branches.
+// Hi patterns are grouped by their number of active units; a group is skipped
+// by one warp-uniform branch when lo plus the group exceeds gamma units.
+// Pass 1 finds the maximum m; pass 2 forms e = 2^(l - m), the moments and the
+// MAP state (the canonically first state with l == m, found by a min over the
+// key (|s| << 16) + 0xFFFF - bitreverse(s)).
 template <int HP, bool ENCODE>
 __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
     constexpr int HB = HP < 5 ? HP : 5;
     constexpr int LB = HP - HB;
     constexpr int NT = 1 << HB;
     constexpr int NLO = 1 << LB;
+    constexpr int LBX = LB > 0 ? LB : 1;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = n < A.N;
     const int64_t nn = valid ? n : 0;
@@ -322,11 +411,15 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
         float pj = A.selp[nn * SEL_STRIDE + j];
         float gjj = __ldg(A.G + (size_t)I[j] * H + I[j]);
         a[j] = lpi + (pj - 0.5f * gjj) * is2;
+        b[j][j] = 0.f;
     }
 #pragma unroll
     for (int i = 0; i < HP; ++i)
 #pragma unroll
-        for (int j = i + 1; j < HP; ++j) b[i][j] = -__ldg(A.G + (size_t)I[i] * H + I[j]) * is2;
+        for (int j = i + 1; j < HP; ++j) {
+            b[i][j] = -__ldg(A.G + (size_t)I[i] * H + I[j]) * is2;
+            b[j][i] = b[i][j];
+        }
 
     float M[NT];
 #pragma unroll
@@ -340,95 +433,73 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
         M[t] = s;
     }
 
-    // -------- pass 1: maximum log-joint
+    // -------- pass 1: maximum log-joint over the valid states
     float m = -INFINITY;
+#pragma unroll 1
     for (int lo = 0; lo < NLO; ++lo) {
         const int cap = gamma - __popc(lo);
         if (cap < 0) continue;
-        float L = 0.f;
-#pragma unroll
-        for (int i = 0; i < LB; ++i) {
-            if ((lo >> i) & 1) {
-                L += a[i];
-#pragma unroll
-                for (int j = i + 1; j < LB; ++j)
-                    if ((lo >> j) & 1) L += b[i][j];
-            }
-        }
-        float c[HB];
-#pragma unroll
-        for (int u = 0; u < HB; ++u) {
-            float v = a[LB + u];
-#pragma unroll
-            for (int i = 0; i < LB; ++i)
-                if ((lo >> i) & 1) v += b[i][LB + u];
-            c[u] = v;
-        }
+        float mk[LBX], L, c[HB];
+        lo_terms<HP, LB, HB>(lo, a, b, mk, L, c);
         float C[NT];
         C[0] = L;
 #pragma unroll
         for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)];
 #pragma unroll
-        for (int t = 0; t < NT; ++t)
-            if (cpopc(t) <= cap) m = fmaxf(m, C[t] + M[t]);
+        for (int k = 0; k <= HB; ++k) {
+            if (k <= cap) {
+#pragma unroll
+                for (int t = 0; t < NT; ++t)
+                    if (cpopc(t) == k) m = fmaxf(m, C[t] + M[t]);
+            }
+        }
     }
 
     // -------- pass 2: exponentials, moments, MAP
     float Z = 0.f;
-    float LL[LB > 0 ? LB : 1][LB > 0 ? LB : 1];
-    float LH[LB > 0 ? LB : 1][HB];
+    float LL[LBX][LBX];
+    float LH[LBX][HB];
     float Gacc[NT];
 #pragma unroll
-    for (int i = 0; i < (LB > 0 ? LB : 1); ++i) {
+    for (int i = 0; i < LBX; ++i) {
 #pragma unroll
-        for (int j = 0; j < (LB > 0 ? LB : 1); ++j) LL[i][j] = 0.f;
+        for (int j = 0; j < LBX; ++j) LL[i][j] = 0.f;
 #pragma unroll
         for (int u = 0; u < HB; ++u) LH[i][u] = 0.f;
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t) Gacc[t] = 0.f;
-    unsigned mapmask = 0xffffffffu;
+    int best = 0x7fffffff;
 
+#pragma unroll 1
     for (int lo = 0; lo < NLO; ++lo) {
         const int cap = gamma - __popc(lo);
         if (cap < 0) continue;
-        float L = 0.f;
-#pragma unroll
-        for (int i = 0; i < LB; ++i) {
-            if ((lo >> i) & 1) {
-                L += a[i];
-#pragma unroll
-                for (int j = i + 1; j < LB; ++j)
-                    if ((lo >> j) & 1) L += b[i][j];
-            }
-        }
-        float c[HB];
-#pragma unroll
-        for (int u = 0; u < HB; ++u) {
-            float v = a[LB + u];
-#pragma unroll
-            for (int i = 0; i < LB; ++i)
-                if ((lo >> i) & 1) v += b[i][LB + u];
-            c[u] = v;
-        }
+        float mk[LBX], L, c[HB];
+        lo_terms<HP, LB, HB>(lo, a, b, mk, L, c);
         float C[NT];
         C[0] = L;
 #pragma unroll
         for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)];
+        const int klo = (__popc(lo) << 16) + 0xFFFF - (int)(__brev((unsigned)lo) >> (32 - HP));
         float e[NT];
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            e[t] = 0.f;
-            if (cpopc(t) <= cap) {
-                float l = C[t] + M[t];
-                e[t] = exp2f(l - m);
-                if (l == m) {
-                    unsigned cand = (unsigned)lo | ((unsigned)t << LB);
-                    if (canon_less(cand, mapmask)) mapmask = cand;
+        for (int t = 0; t < NT; ++t) e[t] = 0.f;
+#pragma unroll
+        for (int k = 0; k <= HB; ++k) {
+            if (k <= cap) {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    if (cpopc(t) == k) {
+                        const float l = C[t] + M[t];
+                        e[t] = fast_ex2(l - m);
+                        const int key = klo + ((cpopc(t) << 16) - crev_hi(t, LB, HP));
+                        best = (l == m) ? min(best, key) : best;
+                    }
                 }
             }
         }
-        // R[u] = sum_{t contains u} e[t]; total by pairwise halving
+        // R[u] = sum_{t contains u} e[t] and the total, by pairwise halving
         float R[HB];
         float Zlo;
         {
@@ -452,44 +523,51 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
         for (int t = 0; t < NT; ++t) Gacc[t] += e[t];
 #pragma unroll
         for (int i = 0; i < LB; ++i) {
-            if ((lo >> i) & 1) {
 #pragma unroll
-                for (int u = 0; u < HB; ++u) LH[i][u] += R[u];
+            for (int u = 0; u < HB; ++u) LH[i][u] = fmaf(mk[i], R[u], LH[i][u]);
+            LL[i][i] = fmaf(mk[i], Zlo, LL[i][i]);
 #pragma unroll
-                for (int j = i; j < LB; ++j)
-                    if ((lo >> j) & 1) LL[i][j] += Zlo;
-            }
+            for (int j = i + 1; j < LB; ++j) LL[i][j] = fmaf(mk[i] * mk[j], Zlo, LL[i][j]);
         }
         Z += Zlo;
     }
 
-    // hi-hi moments from the accumulated hi-pattern weights
-    float HS[HB], HPr[HB][HB];
+    // second moments <s_i s_j> (unnormalised) in one symmetric table
+    float S2[HP][HP];
 #pragma unroll
-    for (int u = 0; u < HB; ++u) {
-        float s = 0.f;
+    for (int i = 0; i < HP; ++i)
 #pragma unroll
-        for (int t = 0; t < NT; ++t)
-            if ((t >> u) & 1) s += Gacc[t];
-        HS[u] = s;
+        for (int j = i; j < HP; ++j) {
+            float v;
+            if (j < LB) {
+                v = LL[i < LB ? i : 0][j < LB ? j : 0];
+            } else if (i < LB) {
+                v = LH[i < LB ? i : 0][j - LB];
+            } else {
+                const int u = i - LB, w = j - LB;
+                float s = 0.f;
 #pragma unroll
-        for (int v = u + 1; v < HB; ++v) {
-            float q = 0.f;
-#pragma unroll
-            for (int t = 0; t < NT; ++t)
-                if (((t >> u) & 1) && ((t >> v) & 1)) q += Gacc[t];
-            HPr[u][v] = q;
+                for (int t = 0; t < NT; ++t)
+                    if (((t >> u) & 1) && ((t >> w) & 1)) s += Gacc[t];
+                v = s;
+            }
+            S2[i][j] = v;
         }
-    }
     const float invZ = 1.f / Z;
     float es[HP];
 #pragma unroll
-    for (int j = 0; j < HP; ++j) es[j] = (j < LB ? LL[j < LB ? j : 0][j < LB ? j : 0] : HS[j >= LB ? j - LB : 0]) * invZ;
+    for (int j = 0; j < HP; ++j) es[j] = S2[j][j] * invZ;
 
-    const double yy = (double)A.yy[nn];
+    const float2 yyv = A.yy[nn];
+    const double yy = (double)yyv.x + (double)yyv.y;
     const double s2 = sigma * sigma;
     const double logp0 = H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2)) - yy / (2.0 * s2);
     const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp0;
+    // MAP state mask from the winning key
+    const unsigned rmask = 0xFFFFu - (unsigned)(best & 0xFFFF);
+    unsigned mapmask = 0u;
+#pragma unroll
+    for (int j = 0; j < HP; ++j) mapmask |= ((rmask >> (HP - 1 - j)) & 1u) << j;
 
     if (ENCODE) {
         if (valid) {
@@ -519,15 +597,9 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
         // sum <s s^T> into the upper triangle of B (I ascending -> I_i < I_j)
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
-            atomicAdd(A.B + (size_t)I[i] * H + I[i], (double)es[i]);
+            double *row = A.B + (size_t)I[i] * H;
 #pragma unroll
-            for (int j = i + 1; j < HP; ++j) {
-                float v;
-                if (j < LB) v = LL[i < LB ? i : 0][j < LB ? j : 0];
-                else if (i < LB) v = LH[i < LB ? i : 0][j - LB >= 0 ? j - LB : 0];
-                else v = HPr[i - LB >= 0 ? i - LB : 0][j - LB >= 0 ? j - LB : 0];
-                atomicAdd(A.B + (size_t)I[i] * H + I[j], (double)(v * invZ));
-            }
+            for (int j = i; j < HP; ++j) atomicAdd(row + I[j], (double)(S2[i][j] * invZ));
         }
     }
     // scalar statistics: warp reduction in FP64, one atomic per warp
@@ -681,7 +753,7 @@ int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t 
     int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_f32", s);
     k_bsc_proj_f32<<<grid, 256, smem, s>>>(Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->sel,
-                                           c->selp, c->yy, c->d_status);
+                                           c->selp, reinterpret_cast<float2 *>(c->yy), c->d_status);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }
@@ -701,7 +773,7 @@ int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_
                       float *mapp_out, float *logz_out, cudaStream_t s) {
     if (N <= 0) return PROSPER_OK;
     StateArgs A;
-    A.sel = c->sel; A.selp = c->selp; A.yy = c->yy; A.G = c->G;
+    A.sel = c->sel; A.selp = c->selp; A.yy = reinterpret_cast<const float2 *>(c->yy); A.G = c->G;
     A.N = N; A.H = c->H; A.D = c->D; A.gamma = c->gamma; A.theta = theta;
     A.es = c->es;
     A.B = st ? st->B : nullptr;

@@ -75,7 +75,7 @@ struct prosper_ctx {
     // per-piece scratch
     int32_t *sel = nullptr;   // chunk x SEL_STRIDE selected latents (ascending)
     float *selp = nullptr;    // chunk x SEL_STRIDE FP32 projections of the selected latents
-    float *yy = nullptr;      // chunk: y^T y
+    float *yy = nullptr;      // chunk x 2: y^T y as an unevaluated sum hi + lo
     float *es = nullptr;      // chunk x SEL_STRIDE posterior means <s> of the selected latents
 
     // M-step workspace (FP64)
