@@ -319,13 +319,14 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
 }
 
 // ----------------------------------------------------------- state kernel
-__host__ __device__ constexpr int cpopc(int x) { return x == 0 ? 0 : (x & 1) + cpopc(x >> 1); }
-__host__ __device__ constexpr int cctz(int x) { return (x & 1) ? 0 : 1 + cctz(x >> 1); }
+// Bit helpers on compile-time-constant patterns: written with intrinsics so that
+// they fold to constants inside unrolled loops (recursive constexpr helpers are
+// not inlined by the device compiler and would run at run time).
+#define cpopc(t) __popc((unsigned)(t))
+#define cctz(t) (__ffs((int)(t)) - 1)
 // sum over the hi units u in t of 2^(HP-1-(LB+u)): the weight of t in the
 // bit-reversed state mask (lower local unit = higher weight).
-__host__ __device__ constexpr int crev_hi(int t, int LB, int HP) {
-    return t == 0 ? 0 : ((t & 1) << (HP - 1 - LB)) + crev_hi(t >> 1, LB + 1, HP);
-}
+#define crev_hi(t, LB, HP) ((int)(__brev((unsigned)(t) << (LB)) >> (32 - (HP))))
 
 __device__ __forceinline__ float fast_ex2(float x) {
     float y;
@@ -352,28 +353,53 @@ struct StateArgs {
 };
 
 // L(lo) = sum_{j in lo} a_j + sum_{i<j in lo} b_ij and c_u(lo) = a_u + sum_{i in lo} b_iu,
-// evaluated branch-free with 0/1 multipliers (fmaf(0, x, s) = s and
-// fmaf(1, x, s) = s + x exactly, so this equals the plain sums).
-template <int HP, int LB, int HB>
-__device__ __forceinline__ void lo_terms(int lo, const float (&a)[HP], const float (&b)[HP][HP],
-                                         float (&mk)[LB > 0 ? LB : 1], float &L, float (&c)[HB]) {
-#pragma unroll
-    for (int i = 0; i < LB; ++i) mk[i] = (float)((lo >> i) & 1);
-    L = 0.f;
-#pragma unroll
-    for (int i = 0; i < LB; ++i) {
-        L = fmaf(mk[i], a[i], L);
-#pragma unroll
-        for (int j = i + 1; j < LB; ++j) L = fmaf(mk[i] * mk[j], b[i][j], L);
+// branch-free with 0/1 multipliers (fmaf(0, x, s) = s and fmaf(1, x, s) = s + x
+// exactly, so these equal the plain sums), then C[t] = L + sum_{u in t} c_u.
+#define PROSPER_LO_TERMS()                                                        \
+    float mk[LBX], C[NT];                                                          \
+    {                                                                              \
+        _Pragma("unroll") for (int i = 0; i < LB; ++i) mk[i] = (float)((lo >> i) & 1); \
+        float L = 0.f;                                                             \
+        _Pragma("unroll") for (int i = 0; i < LB; ++i) {                           \
+            L = fmaf(mk[i], a[i], L);                                              \
+            _Pragma("unroll") for (int j = i + 1; j < LB; ++j)                     \
+                L = fmaf(mk[i] * mk[j], b[i][j], L);                               \
+        }                                                                          \
+        float c[HB];                                                               \
+        _Pragma("unroll") for (int u = 0; u < HB; ++u) {                           \
+            float v = a[LB + u];                                                   \
+            _Pragma("unroll") for (int i = 0; i < LB; ++i) v = fmaf(mk[i], b[i][LB + u], v); \
+            c[u] = v;                                                              \
+        }                                                                          \
+        C[0] = L;                                                                  \
+        _Pragma("unroll") for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)]; \
     }
-#pragma unroll
-    for (int u = 0; u < HB; ++u) {
-        float v = a[LB + u];
-#pragma unroll
-        for (int i = 0; i < LB; ++i) v = fmaf(mk[i], b[i][LB + u], v);
-        c[u] = v;
+
+// Pass 1 body for group K: running maximum.
+#define PROSPER_P1_GROUP(K)                                                        \
+    if ((K) <= HB && (K) <= cap) {                                                 \
+        _Pragma("unroll") for (int t = 0; t < NT; ++t) {                           \
+            if (cpopc(t) == (K)) m = fmaxf(m, C[t] + M[t]);                        \
+        }                                                                          \
     }
-}
+
+// Pass 2 body for group K: e = 2^(l - m) and the MAP key of states with l == m.
+#define PROSPER_P2_GROUP(K)                                                        \
+    if ((K) <= HB) {                                                               \
+        if ((K) <= cap) {                                                          \
+            _Pragma("unroll") for (int t = 0; t < NT; ++t) {                       \
+                if (cpopc(t) == (K)) {                                             \
+                    const float l = C[t] + M[t];                                   \
+                    e[t] = fast_ex2(l - m);                                        \
+                    const int key = klo + ((cpopc(t) << 16) - crev_hi(t, LB, HP)); \
+                    best = min(best, (l == m) ? key : 0x7fffffff);                 \
+                }                                                                  \
+            }                                                                      \
+        } else {                                                                   \
+            _Pragma("unroll") for (int t = 0; t < NT; ++t)                         \
+                if (cpopc(t) == (K)) e[t] = 0.f;                                   \
+        }                                                                          \
+    }
 
 // One thread per data point.  Local units 0..LB-1 ("lo") are enumerated by a
 // warp-uniform loop; units LB..HP-1 ("hi", HB = min(HP,5) of them) are
@@ -439,20 +465,13 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
     for (int lo = 0; lo < NLO; ++lo) {
         const int cap = gamma - __popc(lo);
         if (cap < 0) continue;
-        float mk[LBX], L, c[HB];
-        lo_terms<HP, LB, HB>(lo, a, b, mk, L, c);
-        float C[NT];
-        C[0] = L;
-#pragma unroll
-        for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)];
-#pragma unroll
-        for (int k = 0; k <= HB; ++k) {
-            if (k <= cap) {
-#pragma unroll
-                for (int t = 0; t < NT; ++t)
-                    if (cpopc(t) == k) m = fmaxf(m, C[t] + M[t]);
-            }
-        }
+        PROSPER_LO_TERMS();
+        PROSPER_P1_GROUP(0);
+        PROSPER_P1_GROUP(1);
+        PROSPER_P1_GROUP(2);
+        PROSPER_P1_GROUP(3);
+        PROSPER_P1_GROUP(4);
+        PROSPER_P1_GROUP(5);
     }
 
     // -------- pass 2: exponentials, moments, MAP
@@ -475,30 +494,15 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
     for (int lo = 0; lo < NLO; ++lo) {
         const int cap = gamma - __popc(lo);
         if (cap < 0) continue;
-        float mk[LBX], L, c[HB];
-        lo_terms<HP, LB, HB>(lo, a, b, mk, L, c);
-        float C[NT];
-        C[0] = L;
-#pragma unroll
-        for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)];
+        PROSPER_LO_TERMS();
         const int klo = (__popc(lo) << 16) + 0xFFFF - (int)(__brev((unsigned)lo) >> (32 - HP));
         float e[NT];
-#pragma unroll
-        for (int t = 0; t < NT; ++t) e[t] = 0.f;
-#pragma unroll
-        for (int k = 0; k <= HB; ++k) {
-            if (k <= cap) {
-#pragma unroll
-                for (int t = 0; t < NT; ++t) {
-                    if (cpopc(t) == k) {
-                        const float l = C[t] + M[t];
-                        e[t] = fast_ex2(l - m);
-                        const int key = klo + ((cpopc(t) << 16) - crev_hi(t, LB, HP));
-                        best = (l == m) ? min(best, key) : best;
-                    }
-                }
-            }
-        }
+        PROSPER_P2_GROUP(0);
+        PROSPER_P2_GROUP(1);
+        PROSPER_P2_GROUP(2);
+        PROSPER_P2_GROUP(3);
+        PROSPER_P2_GROUP(4);
+        PROSPER_P2_GROUP(5);
         // R[u] = sum_{t contains u} e[t] and the total, by pairwise halving
         float R[HB];
         float Zlo;
