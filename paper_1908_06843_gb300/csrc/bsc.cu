@@ -741,6 +741,7 @@ int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
         k_transpose<<<tg, tb, 0, s>>>(W, H, D, c->Wd);
         PROSPER_LAUNCH_CHECK();
     }
+    if (c->Wb) return launch_bsc_bf16_prep(c, W, s);
     return PROSPER_OK;
 }
 

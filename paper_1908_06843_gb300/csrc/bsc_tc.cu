@@ -1,5 +1,444 @@
-// bsc_tc.cu -- BF16 tcgen05 projection for BSC preselection.
+// bsc_tc.cu -- BSC preselection with the projection W^T y on the tcgen05 tensor
+// cores in BF16 (FP32 accumulation in tensor memory), then the H' selected
+// projections recomputed in FP32 ("rescore").
+//
+// Method (paper Sec. 2-3: truncated posteriors with H' candidates per point):
+// the preselection score of latent h is W_h^T y / ||W_h||.  Here the N x H
+// score matrix is produced 128 points at a time by one tcgen05.mma chain
+// (M = 128 points, N = H latents, K = D pixels) whose A operand is the Y tile
+// converted to BF16 in shared memory and whose B operand is the BF16 copy of W
+// resident in shared memory for the whole persistent CTA.  The accumulator
+// tile (128 lanes x H columns, FP32) is read back with tcgen05.ld, staged in
+// shared memory 64 points at a time, and every warp takes the top-H' of its
+// points exactly as the FP32 path does (ties to the lower h).  The H' selected
+// projections are then recomputed in FP32 from the FP32 Y and W, so BF16 only
+// decides which latents are candidates.
+//
+// Shared memory (1024-byte aligned, K-major, 128-byte swizzle, 8-row core groups):
+//   W  : D/64 K-blocks, each H rows x 128 B    (H*D*2 bytes, resident)
+//   Y  : D/64 K-blocks, each 128 rows x 128 B  (128*D*2 bytes), reused after the
+//        MMA as the FP32 projection stage P (64 rows x H floats, 16-byte chunks
+//        XOR-swizzled by row so row-wise stores and column reads are conflict-free)
 #include "internal.cuh"
+
+#include <cuda_bf16.h>
+
 namespace prosper {
-int launch_bsc_proj_bf16(prosper_ctx *, const float *, const float *, int64_t, cudaStream_t) { set_error("BF16 path not built yet"); return PROSPER_EINVAL; }
+namespace {
+
+constexpr int TM = 128;                       // points per tile (MMA M)
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded mbarrier wait: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ unsigned long long gtime_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// Wait for the phase with the given parity; gives up after limit_ns (returns false).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+    const unsigned long long t0 = gtime_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if (gtime_ns() - t0 > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading-dimension offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;           // stride between 8-row groups
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ unsigned ordered_key(float s) {
+    unsigned b = __float_as_uint(s);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// index of float (row, col) in the swizzled projection stage (rows of H floats)
+__device__ __forceinline__ int pidx(int row, int col, int H) {
+    return row * H + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
+}
+
+// byte offset of the 16-byte chunk c (8 BF16 values, d = 8c .. 8c+7) of row r in a
+// K-major 128-byte-swizzled operand with `rows` rows per 64-wide K-block
+__device__ __forceinline__ uint32_t opnd_off(int r, int c, int rows) {
+    const int kb = c >> 3, ch = c & 7;
+    return (uint32_t)(kb * rows * 128 + r * 128 + ((ch ^ (r & 7)) << 4));
+}
+
+__global__ void __launch_bounds__(256, 1)
+k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
+                const uint16_t *__restrict__ Wimg, const float *__restrict__ rnorm, int64_t N,
+                int D, int H, int Hp, uint32_t tmem_cols, int32_t *__restrict__ sel_out,
+                float *__restrict__ selp_out, float2 *__restrict__ yy_out,
+                unsigned *__restrict__ status) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char *sbase = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    const size_t wbytes = (size_t)H * D * 2;
+    unsigned char *Wsm = sbase;
+    unsigned char *Ysm = sbase + ((wbytes + 1023) & ~(size_t)1023);
+    float *Psm = reinterpret_cast<float *>(Ysm);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nchunk = D / 8;                 // 16-byte chunks per row
+    const int nkb = D / 64;
+    const int64_t ntiles = (N + TM - 1) / TM;
+    const uint32_t idesc = idesc_bf16(TM, H);
+    const uint32_t bar = smem_u32(&mbar);
+
+    // resident BF16 dictionary (already in the operand image layout)
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(Wimg);
+        uint4 *dst = reinterpret_cast<uint4 *>(Wsm);
+        for (size_t i = tid; i < wbytes / 16; i += 256) dst[i] = __ldg(src + i);
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_slot)), "r"(tmem_cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    float rn[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int h = lane + 32 * j;
+        rn[j] = h < H ? rnorm[h] : 0.f;
+    }
+
+    uint32_t phase = 0;
+    bool aborted = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+        const int64_t n0 = tile * TM;
+        // ---- Y tile -> BF16 operand; exact y^T y on the way
+        for (int r = warp; r < TM; r += 8) {
+            const int64_t n = n0 + r;
+            float hi = 0.f, lo = 0.f;
+            for (int c = lane; c < nchunk; c += 32) {
+                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                if (n < N) {
+                    const float4 *row = reinterpret_cast<const float4 *>(Y + n * D + 8 * c);
+                    v0 = __ldg(row);
+                    v1 = __ldg(row + 1);
+                }
+                const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float p = v[k] * v[k];
+                    const float pe = fmaf(v[k], v[k], -p);
+                    const float s = hi + p;
+                    const float bb = s - hi;
+                    lo += ((hi - (s - bb)) + (p - bb)) + pe;
+                    hi = s;
+                }
+                __nv_bfloat162 b0 = __floats2bfloat162_rn(v0.x, v0.y);
+                __nv_bfloat162 b1 = __floats2bfloat162_rn(v0.z, v0.w);
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(v1.x, v1.y);
+                __nv_bfloat162 b3 = __floats2bfloat162_rn(v1.z, v1.w);
+                uint4 pk;
+                pk.x = *reinterpret_cast<uint32_t *>(&b0);
+                pk.y = *reinterpret_cast<uint32_t *>(&b1);
+                pk.z = *reinterpret_cast<uint32_t *>(&b2);
+                pk.w = *reinterpret_cast<uint32_t *>(&b3);
+                *reinterpret_cast<uint4 *>(Ysm + opnd_off(r, c, TM)) = pk;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+                const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+                const float s = hi + h2;
+                const float bb = s - hi;
+                lo = lo + l2 + ((hi - (s - bb)) + (h2 - bb));
+                hi = s;
+            }
+            if (lane == 0 && n < N) {
+                yy_out[n] = make_float2(hi, lo);
+                if (!isfinite(hi)) atomicOr(status, ST_NONFINITE);
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        // ---- projection tile on the tensor cores
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t ya = smem_u32(Ysm), wa = smem_u32(Wsm);
+            for (int kb = 0; kb < nkb; ++kb)
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t a = desc_sw128(ya + kb * TM * 128 + ks * 32);
+                    const uint64_t b = desc_sw128(wa + kb * H * 128 + ks * 32);
+                    umma_bf16(tmem, a, b, idesc, (kb | ks) != 0);
+                }
+            umma_commit(bar);
+        }
+        const bool ok = mbar_wait(bar, phase, kWaitNs);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+            aborted = true;
+            break;
+        }
+        tc_fence_after();
+
+        // ---- two halves of 64 points: TMEM -> shared P -> selection + FP32 rescore
+        for (int half = 0; half < 2; ++half) {
+            const int q = warp & 3;                 // TMEM lane quadrant of this warp
+            if ((q >> 1) == half) {
+                const int prow = (q & 1) * 32 + lane;   // row within the half
+                const int cbeg = (warp < 4) ? 0 : H / 2;
+                const int cend = (warp < 4) ? H / 2 : H;
+                for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                    for (int k = 0; k < 16; k += 4)
+                        *reinterpret_cast<float4 *>(&Psm[pidx(prow, c0 + k, H)]) =
+                            make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            for (int i = 0; i < 8; ++i) {
+                const int p = warp * 8 + i;
+                const int64_t n = n0 + 64 * half + p;
+                if (n >= N) break;
+                unsigned key[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int h = lane + 32 * j;
+                    key[j] = h < H ? ordered_key(Psm[pidx(p, h, H)] * rn[j]) : 0u;
+                }
+                // top-Hp, exact ties to the lower h (same rule as the FP32 path)
+                int sel[PROSPER_MAX_HPRIME];
+                {
+                    unsigned lk = key[0];
+                    int lj = 0;
+#pragma unroll
+                    for (int j = 1; j < 8; ++j)
+                        if (key[j] > lk) { lk = key[j]; lj = j; }
+#pragma unroll
+                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                        if (r < Hp) {
+                            const unsigned wmax = __reduce_max_sync(0xffffffffu, lk);
+                            const unsigned code = (lk == wmax) ? (unsigned)(lj * 32 + lane) : 0xffffffffu;
+                            const unsigned hw = __reduce_min_sync(0xffffffffu, code);
+                            sel[r] = (int)hw;
+                            if ((int)(hw & 31u) == lane) {
+                                const int jw = (int)(hw >> 5);
+#pragma unroll
+                                for (int j = 0; j < 8; ++j)
+                                    if (j == jw) key[j] = 0u;
+                                lk = key[0];
+                                lj = 0;
+#pragma unroll
+                                for (int j = 1; j < 8; ++j)
+                                    if (key[j] > lk) { lk = key[j]; lj = j; }
+                            }
+                        } else {
+                            sel[r] = 0x7fffffff;
+                        }
+                    }
+                }
+                // FP32 rescore: partial dot products over this lane's d, then a
+                // transposed warp reduction (16 slots -> one total per lane pair)
+                float v[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[r] = 0.f;
+                const float *yrow = Y + n * D;
+                for (int c = lane; c < nchunk; c += 32) {
+                    const float4 y0 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c));
+                    const float4 y1 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c + 4));
+#pragma unroll
+                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                        if (r < Hp) {
+                            const float *wrow = Wt + (size_t)sel[r] * D + 8 * c;
+                            const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wrow));
+                            const float4 w1 = __ldg(reinterpret_cast<const float4 *>(wrow + 4));
+                            float s = v[r];
+                            s = fmaf(y0.x, w0.x, s); s = fmaf(y0.y, w0.y, s);
+                            s = fmaf(y0.z, w0.z, s); s = fmaf(y0.w, w0.w, s);
+                            s = fmaf(y1.x, w1.x, s); s = fmaf(y1.y, w1.y, s);
+                            s = fmaf(y1.z, w1.z, s); s = fmaf(y1.w, w1.w, s);
+                            v[r] = s;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const bool up = (lane & 16) != 0;
+                    const float send = up ? v[k] : v[k + 8];
+                    const float keep = up ? v[k + 8] : v[k];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const bool up = (lane & 8) != 0;
+                    const float send = up ? v[k] : v[k + 4];
+                    const float keep = up ? v[k + 4] : v[k];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const bool up = (lane & 4) != 0;
+                    const float send = up ? v[k] : v[k + 2];
+                    const float keep = up ? v[k + 2] : v[k];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                {
+                    const bool up = (lane & 2) != 0;
+                    const float send = up ? v[0] : v[1];
+                    const float keep = up ? v[1] : v[0];
+                    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                }
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                // this lane now holds the total of round index jr
+                const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                               ((lane >> 1) & 1);
+                int myh = 0x7fffffff;
+#pragma unroll
+                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
+                    if (r == lane) myh = sel[r];
+                int rank = 0;
+#pragma unroll
+                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) rank += (sel[r] < myh) ? 1 : 0;
+                const int h_jr = __shfl_sync(0xffffffffu, myh, jr & 31);
+                const int rank_jr = __shfl_sync(0xffffffffu, rank, jr & 31);
+                if ((lane & 1) == 0 && jr < Hp) {
+                    sel_out[n * SEL_STRIDE + rank_jr] = h_jr;
+                    selp_out[n * SEL_STRIDE + rank_jr] = v[0];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// BF16 image of W in the operand layout above: K-block kb holds rows h of 128 B
+// (d = 64 kb .. 64 kb + 63), 16-byte chunk c stored at chunk position c ^ (h & 7).
+__global__ void k_w_image(const float *__restrict__ Wt, int H, int D, uint16_t *__restrict__ img) {
+    const int64_t total = (int64_t)H * D;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int h = (int)(i / D), d = (int)(i % D);
+        const int kb = d >> 6, ch = (d & 63) >> 3, w = d & 7;
+        const size_t off = (size_t)kb * H * 64 + (size_t)h * 64 + (size_t)((ch ^ (h & 7)) * 8 + w);
+        const __nv_bfloat16 b = __float2bfloat16_rn(Wt[i]);
+        img[off] = *reinterpret_cast<const uint16_t *>(&b);
+    }
+}
+
+}  // namespace
+
+size_t bf16_smem_bytes(int D, int H) {
+    const size_t w = ((size_t)H * D * 2 + 1023) & ~(size_t)1023;
+    const size_t y = std::max((size_t)TM * D * 2, (size_t)64 * H * 4);
+    return 1024 + w + y;
+}
+
+int launch_bsc_bf16_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
+    TraceScope tr(c, "bsc_w_image", s);
+    k_w_image<<<c->num_sms * 2, 256, 0, s>>>(W, c->H, c->D, c->Wb);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t N, cudaStream_t s) {
+    if (N <= 0) return PROSPER_OK;
+    if ((reinterpret_cast<uintptr_t>(Y) & 15) || (reinterpret_cast<uintptr_t>(W) & 15)) {
+        set_error("BF16 path needs 16-byte aligned Y and W");
+        return PROSPER_EINVAL;
+    }
+    const size_t smem = bf16_smem_bytes(c->D, c->H);
+    static size_t attr = 0;
+    if (smem > attr) {
+        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_bsc_proj_bf16,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = smem;
+    }
+    uint32_t cols = 32;
+    while ((int)cols < c->H) cols <<= 1;
+    const int64_t ntiles = (N + TM - 1) / TM;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
+    TraceScope tr(c, "bsc_proj_bf16", s);
+    k_bsc_proj_bf16<<<grid, 256, smem, s>>>(Y, W, c->Wb, c->rnorm, N, c->D, c->H, c->Hp, cols,
+                                            c->sel, c->selp, reinterpret_cast<float2 *>(c->yy),
+                                            c->d_status);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+}  // namespace prosper

@@ -184,3 +184,69 @@ def test_full_size_sampled(orc):
     a = (orc.BSC, Ys, Wt, 4 / 256, 0.2, 10, 5, sel)
     check_points(orc, *a, enc["s_mean"].cpu().numpy()[idx], ref["smean"], "s_mean")
     check_points(orc, *a, enc["map_p"].cpu().numpy()[idx], ref["map_p"], "map_p")
+
+
+# ---------------------------------------------------------------- BF16 form
+def _bf16_tau(Y, Wt):
+    """Bound on the BF16 score error: both operands rounded to BF16 (unit
+    roundoff 2^-8 each), so |score_bf16 - score| <= 2^-7 sum_d |W_hd y_d| / |W_h|
+    (x1.01 for the FP32 accumulation); two scores can move towards each other."""
+    A = np.abs(np.asarray(Wt, np.float64))
+    nrm = np.linalg.norm(np.asarray(Wt, np.float64), axis=1)
+
+    def tau(n, sc):
+        b = (A @ np.abs(np.asarray(Y[n], np.float64))) / np.where(nrm > 0, nrm, 1.0)
+        return 2.0 * (2.0 ** -7) * 1.01 * np.max(b) + 1e-6
+    return tau
+
+
+def test_bf16_gabor_small_n(orc):
+    """BF16 tcgen05 projection + FP32 rescore, D=H=256, H'=10, gamma=5, N=2050
+    (17 tiles of 128 points, ragged tail): selections optimal within the BF16
+    bound, statistics equal to the oracle's on the GPU's selections."""
+    d = synth.gabor(N=2050, seed=1002)
+    Y32 = d["Y"]
+    Wt = d["Wt"].astype(np.float32).astype(np.float64)
+    _, _, _, n_diff, _ = run_parity(orc, Y32, Wt, 4 / 256, 0.2, 10, 5, precision=1,
+                                    tau_fn=_bf16_tau(Y32, Wt))
+    print(f"BF16 selection differs from FP64 on {n_diff} of {len(Y32)} points")
+    p = synth.init_bsc(d["Y"], 256, seed=2002, pi=0.02, normalise=True)
+    Wi = p["Wt"].astype(np.float32).astype(np.float64)
+    run_parity(orc, Y32, Wi, p["pi"], p["sigma"], 10, 5, precision=1, tau_fn=_bf16_tau(Y32, Wi))
+
+
+@pytest.mark.parametrize("N", [1, 127, 128, 129, 300])
+def test_bf16_tile_edges(orc, N):
+    d = synth.gabor(N=N, seed=78, H=64)
+    Wt = d["Wt"].astype(np.float32).astype(np.float64)
+    run_parity(orc, d["Y"], Wt, 0.05, 0.3, 7, 3, precision=1, tau_fn=_bf16_tau(d["Y"], Wt))
+
+
+def test_bf16_matches_fp32_form_where_selection_agrees(orc):
+    """Where BF16 and FP32 pick the same candidates the encodings coincide
+    (the rescore is FP32), and the full-size E-step statistics agree."""
+    from paper_1908_06843_gb300 import Context
+    d = synth.gabor(N=200_000, seed=1002)
+    Wt = d["Wt"].astype(np.float32)
+    dev = torch.device("cuda")
+    W = torch.tensor(Wt, device=dev)
+    theta = torch.tensor([4 / 256, 0.2, 0, 0], dtype=torch.float64, device=dev)
+    Y = torch.tensor(d["Y"], device=dev)
+    outs, stats = [], []
+    for prec in (0, 1):
+        ctx = Context(0, 256, 256, 10, 5, prec)
+        P = ctx.params(W, theta)
+        st = ctx.alloc_stats()
+        ctx.estep(P, Y, st)
+        outs.append(ctx.encode(P, Y))
+        stats.append(torch_stats_to_numpy(st))
+    torch.cuda.synchronize()
+    same = torch.all(outs[0]["sel"] == outs[1]["sel"], dim=1)
+    frac = float(same.float().mean())
+    assert frac > 0.99, frac
+    m = same
+    assert float((outs[0]["s_mean"][m] - outs[1]["s_mean"][m]).abs().max()) == 0.0
+    assert float((outs[0]["logZ"][m] - outs[1]["logZ"][m]).abs().max()) <= 1e-4
+    # statistics differ only through the near-tie points
+    assert relfro(stats[1]["B"], stats[0]["B"]) <= 1e-3
+    assert abs(stats[1]["scal"][0] - stats[0]["scal"][0]) <= 1e-4 * abs(stats[0]["scal"][0])
