@@ -57,7 +57,7 @@ extern "C" {
 
 /* Limits.  BSC/MCA: 1 <= Hprime <= 10; GSC: Hprime <= 10 and gamma <= 3;
  * 0 <= gamma <= Hprime <= H; BSC/MCA/GSC H <= 256; D <= 1024.
- * PROSPER_BF16_RESCORE additionally needs D % 64 == 0, H % 32 == 0 and
+ * PROSPER_BF16_RESCORE additionally needs D % 64 == 0, H % 64 == 0 and
  * 2*H*D + 256*max(D, H) <= 226 KB (the BF16 dictionary and one operand tile
  * stay in shared memory), e.g. D = H = 256. */
 #define PROSPER_MAX_HPRIME 10

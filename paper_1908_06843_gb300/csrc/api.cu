@@ -157,8 +157,8 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
         return PROSPER_EINVAL;
     }
     if (precision == PROSPER_BF16_RESCORE &&
-        (model != PROSPER_BSC || D % 64 != 0 || H % 32 != 0 || bf16_smem_bytes(D, H) > 227 * 1024)) {
-        set_error("BF16_RESCORE needs BSC, D %% 64 == 0, H %% 32 == 0 and 2HD + 256 max(D, H) <= 226 KB");
+        (model != PROSPER_BSC || D % 64 != 0 || H % 64 != 0 || bf16_smem_bytes(D, H) > 227 * 1024)) {
+        set_error("BF16_RESCORE needs BSC, D %% 64 == 0, H %% 64 == 0 and 2HD + 256 max(D, H) <= 226 KB");
         return PROSPER_EINVAL;
     }
     if (max_points <= 0) max_points = 1 << 20;

@@ -635,10 +635,10 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
 // points and keeps At[:, slice] in shared memory.  Per 256-point chunk the
 // (point, <s>) pairs are bucketed by latent h; warp w then owns latents
 // h = w, w+8, ... so every shared-memory row has a single writer.
-constexpr int AT = 256;   // points per chunk
+constexpr int AT = 128;   // points per chunk
 constexpr int AD = 64;    // d per slice
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
 k_astat(const float *__restrict__ Y, const int32_t *__restrict__ sel, const float *__restrict__ es,
         int64_t N, int D, int H, int Hp, int64_t pts_per_cta, double *__restrict__ At) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -665,10 +665,20 @@ k_astat(const float *__restrict__ Y, const int32_t *__restrict__ sel, const floa
             atomicAdd(&cnt[sel[(c0 + p) * SEL_STRIDE + j]], 1);
         }
         // Y slice of the chunk
-        for (int i = tid; i < AT * AD; i += 256) {
-            int p = i / AD, c = i - p * AD;
-            int d = d0 + c;
-            Ys[i] = (p < np && d < D) ? Y[(c0 + p) * D + d] : 0.f;
+        if ((D % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+            for (int i = tid; i < AT * AD / 4; i += 256) {
+                const int p = i / (AD / 4), c = (i - p * (AD / 4)) * 4;
+                const int d = d0 + c;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (p < np && d < D) v = __ldg(reinterpret_cast<const float4 *>(Y + (c0 + p) * D + d));
+                *reinterpret_cast<float4 *>(&Ys[p * AD + c]) = v;
+            }
+        } else {
+            for (int i = tid; i < AT * AD; i += 256) {
+                int p = i / AD, c = i - p * AD;
+                int d = d0 + c;
+                Ys[i] = (p < np && d < D) ? Y[(c0 + p) * D + d] : 0.f;
+            }
         }
         __syncthreads();
         if (warp == 0) {   // exclusive scan of cnt -> off
@@ -697,9 +707,22 @@ k_astat(const float *__restrict__ Y, const int32_t *__restrict__ sel, const floa
         }
         __syncthreads();
         for (int h = warp; h < H; h += 8) {
-            float a0 = 0.f, a1 = 0.f;
+            // four independent accumulator pairs keep the shared-memory loads in flight
+            float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f, c0 = 0.f, c1 = 0.f, d0 = 0.f, d1 = 0.f;
             const int e1 = off[h + 1];
-            for (int e = off[h]; e < e1; ++e) {
+            int e = off[h];
+            for (; e + 4 <= e1; e += 4) {
+                const float v0 = lv[e], v1 = lv[e + 1], v2 = lv[e + 2], v3 = lv[e + 3];
+                const float2 y0 = *reinterpret_cast<const float2 *>(&Ys[ln[e] * AD + 2 * lane]);
+                const float2 y1 = *reinterpret_cast<const float2 *>(&Ys[ln[e + 1] * AD + 2 * lane]);
+                const float2 y2 = *reinterpret_cast<const float2 *>(&Ys[ln[e + 2] * AD + 2 * lane]);
+                const float2 y3 = *reinterpret_cast<const float2 *>(&Ys[ln[e + 3] * AD + 2 * lane]);
+                a0 = fmaf(v0, y0.x, a0); a1 = fmaf(v0, y0.y, a1);
+                b0 = fmaf(v1, y1.x, b0); b1 = fmaf(v1, y1.y, b1);
+                c0 = fmaf(v2, y2.x, c0); c1 = fmaf(v2, y2.y, c1);
+                d0 = fmaf(v3, y3.x, d0); d1 = fmaf(v3, y3.y, d1);
+            }
+            for (; e < e1; ++e) {
                 const float v = lv[e];
                 const float2 y = *reinterpret_cast<const float2 *>(&Ys[ln[e] * AD + 2 * lane]);
                 a0 = fmaf(v, y.x, a0);
@@ -707,8 +730,8 @@ k_astat(const float *__restrict__ Y, const int32_t *__restrict__ sel, const floa
             }
             float2 *dst = reinterpret_cast<float2 *>(&Apart[h * AD + 2 * lane]);
             float2 cur = *dst;
-            cur.x += a0;
-            cur.y += a1;
+            cur.x += (a0 + b0) + (c0 + d0);
+            cur.y += (a1 + b1) + (c1 + d1);
             *dst = cur;
         }
         __syncthreads();
@@ -813,7 +836,7 @@ int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStre
         attr_smem = smem;
     }
     const int slices = (D + AD - 1) / AD;
-    int ranges = std::max(1, c->num_sms / slices);
+    int ranges = std::max(1, 2 * c->num_sms / slices);
     int64_t per = (N + ranges - 1) / ranges;
     per = ((per + AT - 1) / AT) * AT;
     ranges = (int)((N + per - 1) / per);

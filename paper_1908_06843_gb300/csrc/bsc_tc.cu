@@ -27,6 +27,7 @@ namespace prosper {
 namespace {
 
 constexpr int TM = 128;                       // points per tile (MMA M)
+constexpr int NW = 16;                        // warps per CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded mbarrier wait: 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -122,7 +123,7 @@ __device__ __forceinline__ uint32_t opnd_off(int r, int c, int rows) {
     return (uint32_t)(kb * rows * 128 + r * 128 + ((ch ^ (r & 7)) << 4));
 }
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(NW * 32, 1)
 k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 const uint16_t *__restrict__ Wimg, const float *__restrict__ rnorm, int64_t N,
                 int D, int H, int Hp, uint32_t tmem_cols, int32_t *__restrict__ sel_out,
@@ -149,7 +150,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(Wimg);
         uint4 *dst = reinterpret_cast<uint4 *>(Wsm);
-        for (size_t i = tid; i < wbytes / 16; i += 256) dst[i] = __ldg(src + i);
+        for (size_t i = tid; i < wbytes / 16; i += NW * 32) dst[i] = __ldg(src + i);
     }
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -178,7 +179,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
         const int64_t n0 = tile * TM;
         // ---- Y tile -> BF16 operand; exact y^T y on the way
-        for (int r = warp; r < TM; r += 8) {
+        for (int r = warp; r < TM; r += NW) {
             const int64_t n = n0 + r;
             float hi = 0.f, lo = 0.f;
             for (int c = lane; c < nchunk; c += 32) {
@@ -252,8 +253,9 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
             const int q = warp & 3;                 // TMEM lane quadrant of this warp
             if ((q >> 1) == half) {
                 const int prow = (q & 1) * 32 + lane;   // row within the half
-                const int cbeg = (warp < 4) ? 0 : H / 2;
-                const int cend = (warp < 4) ? H / 2 : H;
+                const int part = warp >> 2;             // 4 warps share a quadrant: H/4 columns each
+                const int cbeg = part * (H / 4);
+                const int cend = cbeg + H / 4;
                 for (int c0 = cbeg; c0 < cend; c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
@@ -265,8 +267,8 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
             }
             tc_fence_before();
             __syncthreads();
-            for (int i = 0; i < 8; ++i) {
-                const int p = warp * 8 + i;
+            for (int i = 0; i < 64 / NW; ++i) {
+                const int p = warp * (64 / NW) + i;
                 const int64_t n = n0 + 64 * half + p;
                 if (n >= N) break;
                 unsigned key[8];
@@ -378,6 +380,11 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
             __syncthreads();
         }
     }
+    if (aborted && tid == 0) {
+        // give the MMA chain that timed out one more bounded chance to finish
+        // before its tensor memory is released
+        mbar_wait(bar, phase ^ 1u, kWaitNs / 2);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -434,7 +441,7 @@ int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t
     const int64_t ntiles = (N + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_bf16", s);
-    k_bsc_proj_bf16<<<grid, 256, smem, s>>>(Y, W, c->Wb, c->rnorm, N, c->D, c->H, c->Hp, cols,
+    k_bsc_proj_bf16<<<grid, NW * 32, smem, s>>>(Y, W, c->Wb, c->rnorm, N, c->D, c->H, c->Hp, cols,
                                             c->sel, c->selp, reinterpret_cast<float2 *>(c->yy),
                                             c->d_status);
     PROSPER_LAUNCH_CHECK();
