@@ -17,6 +17,7 @@
 //   log p(s,y) - log p(0,y) = |s| log(pi/(1-pi)) + (s^T p - s^T G_II s / 2) / sigma^2
 // with p = W_I^T y.  Kernels work in base 2 (all terms times log2 e).
 #include "internal.cuh"
+#include "topk.cuh"
 
 #include <cmath>
 
@@ -70,45 +71,6 @@ __global__ void k_transpose(const float *__restrict__ Wt, int H, int D, float *_
     }
 }
 
-// ------------------------------------------------- selection (warp per point)
-__device__ __forceinline__ unsigned ordered_key(float s) {
-    unsigned b = __float_as_uint(s);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-// Top-Hp of the scores of one point held 8 per lane (h = lane + 32 j), exact
-// ties to the lower h.  Returns the selected h of round r in sel[r] (warp-uniform).
-template <int HPMAX>
-__device__ __forceinline__ void warp_topk(unsigned key[8], int Hp, int sel[HPMAX], int lane) {
-    unsigned lk = key[0];
-    int lj = 0;
-#pragma unroll
-    for (int j = 1; j < 8; ++j)
-        if (key[j] > lk) { lk = key[j]; lj = j; }
-#pragma unroll
-    for (int r = 0; r < HPMAX; ++r) {
-        if (r < Hp) {
-            unsigned wmax = __reduce_max_sync(0xffffffffu, lk);
-            unsigned code = (lk == wmax) ? (unsigned)(lj * 32 + lane) : 0xffffffffu;
-            unsigned hw = __reduce_min_sync(0xffffffffu, code);
-            sel[r] = (int)hw;
-            if ((int)(hw & 31u) == lane) {
-                int jw = (int)(hw >> 5);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (j == jw) key[j] = 0u;
-                lk = key[0];
-                lj = 0;
-#pragma unroll
-                for (int j = 1; j < 8; ++j)
-                    if (key[j] > lk) { lk = key[j]; lj = j; }
-            }
-        } else {
-            sel[r] = 0x7fffffff;
-        }
-    }
-}
-
 // ------------------------------------------------ FP32 projection + selection
 constexpr int PT = 64;        // points per tile
 constexpr int PK = 32;        // d per k-chunk
@@ -119,6 +81,7 @@ struct ProjSmem {
     float Ys[2][PK][PT];      // 16 KB  (d-major so a thread reads 8 points with 2 LDS.128)
     float Ws[2][PK][PH];      // 64 KB
     float Ps[PT][PS];         // 66.5 KB
+    unsigned topk[8][64];     // per-warp selection scratch
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
@@ -293,17 +256,10 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 int h = lane + 32 * j;
-                key[j] = h < H ? ordered_key(sm.Ps[p][h] * rn[j]) : 0u;
+                key[j] = h < H ? score_key(sm.Ps[p][h] * rn[j]) : 0u;
             }
-            int sel[PROSPER_MAX_HPRIME];
-            warp_topk<PROSPER_MAX_HPRIME>(key, Hp, sel, lane);
-            int myh = 0x7fffffff;
-#pragma unroll
-            for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
-                if (r == lane) myh = sel[r];
-            int rank = 0;
-#pragma unroll
-            for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) rank += (sel[r] < myh) ? 1 : 0;
+            const int myh = warp_topk(key, Hp, lane, sm.topk[warp]);
+            const int rank = topk_rank(myh, Hp, lane);
             if (lane < Hp) {
                 sel_out[n * SEL_STRIDE + rank] = myh;
                 selp_out[n * SEL_STRIDE + rank] = sm.Ps[p][myh];

@@ -20,6 +20,7 @@
 //        MMA as the FP32 projection stage P (64 rows x H floats, 16-byte chunks
 //        XOR-swizzled by row so row-wise stores and column reads are conflict-free)
 #include "internal.cuh"
+#include "topk.cuh"
 
 #include <cuda_bf16.h>
 
@@ -106,11 +107,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ unsigned ordered_key(float s) {
-    unsigned b = __float_as_uint(s);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
 // index of float (row, col) in the swizzled projection stage (rows of H floats)
 __device__ __forceinline__ int pidx(int row, int col, int H) {
     return row * H + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
@@ -132,6 +128,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_slot;
+    __shared__ unsigned topk_scratch[NW][64];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *sbase = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const size_t wbytes = (size_t)H * D * 2;
@@ -181,7 +178,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
         // ---- Y tile -> BF16 operand; exact y^T y on the way
         for (int r = warp; r < TM; r += NW) {
             const int64_t n = n0 + r;
-            float hi = 0.f, lo = 0.f;
+            float sq = 0.f;
             for (int c = lane; c < nchunk; c += 32) {
                 float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
                 if (n < N) {
@@ -189,16 +186,10 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                     v0 = __ldg(row);
                     v1 = __ldg(row + 1);
                 }
-                const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const float p = v[k] * v[k];
-                    const float pe = fmaf(v[k], v[k], -p);
-                    const float s = hi + p;
-                    const float bb = s - hi;
-                    lo += ((hi - (s - bb)) + (p - bb)) + pe;
-                    hi = s;
-                }
+                sq = fmaf(v0.x, v0.x, sq); sq = fmaf(v0.y, v0.y, sq);
+                sq = fmaf(v0.z, v0.z, sq); sq = fmaf(v0.w, v0.w, sq);
+                sq = fmaf(v1.x, v1.x, sq); sq = fmaf(v1.y, v1.y, sq);
+                sq = fmaf(v1.z, v1.z, sq); sq = fmaf(v1.w, v1.w, sq);
                 __nv_bfloat162 b0 = __floats2bfloat162_rn(v0.x, v0.y);
                 __nv_bfloat162 b1 = __floats2bfloat162_rn(v0.z, v0.w);
                 __nv_bfloat162 b2 = __floats2bfloat162_rn(v1.x, v1.y);
@@ -211,17 +202,10 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 *reinterpret_cast<uint4 *>(Ysm + opnd_off(r, c, TM)) = pk;
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-                const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-                const float s = hi + h2;
-                const float bb = s - hi;
-                lo = lo + l2 + ((hi - (s - bb)) + (h2 - bb));
-                hi = s;
-            }
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (lane == 0 && n < N) {
-                yy_out[n] = make_float2(hi, lo);
-                if (!isfinite(hi)) atomicOr(status, ST_NONFINITE);
+                yy_out[n] = make_float2(sq, 0.f);
+                if (!isfinite(sq)) atomicOr(status, ST_NONFINITE);
             }
         }
         fence_proxy_async();
@@ -275,39 +259,10 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int h = lane + 32 * j;
-                    key[j] = h < H ? ordered_key(Psm[pidx(p, h, H)] * rn[j]) : 0u;
+                    key[j] = h < H ? score_key(Psm[pidx(p, h, H)] * rn[j]) : 0u;
                 }
                 // top-Hp, exact ties to the lower h (same rule as the FP32 path)
-                int sel[PROSPER_MAX_HPRIME];
-                {
-                    unsigned lk = key[0];
-                    int lj = 0;
-#pragma unroll
-                    for (int j = 1; j < 8; ++j)
-                        if (key[j] > lk) { lk = key[j]; lj = j; }
-#pragma unroll
-                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                        if (r < Hp) {
-                            const unsigned wmax = __reduce_max_sync(0xffffffffu, lk);
-                            const unsigned code = (lk == wmax) ? (unsigned)(lj * 32 + lane) : 0xffffffffu;
-                            const unsigned hw = __reduce_min_sync(0xffffffffu, code);
-                            sel[r] = (int)hw;
-                            if ((int)(hw & 31u) == lane) {
-                                const int jw = (int)(hw >> 5);
-#pragma unroll
-                                for (int j = 0; j < 8; ++j)
-                                    if (j == jw) key[j] = 0u;
-                                lk = key[0];
-                                lj = 0;
-#pragma unroll
-                                for (int j = 1; j < 8; ++j)
-                                    if (key[j] > lk) { lk = key[j]; lj = j; }
-                            }
-                        } else {
-                            sel[r] = 0x7fffffff;
-                        }
-                    }
-                }
+                const int myh = warp_topk(key, Hp, lane, topk_scratch[warp]);
                 // FP32 rescore: partial dot products over this lane's d, then a
                 // transposed warp reduction (16 slots -> one total per lane pair)
                 float v[16];
@@ -319,8 +274,9 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                     const float4 y1 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c + 4));
 #pragma unroll
                     for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                        const int hr = __shfl_sync(0xffffffffu, myh, r);
                         if (r < Hp) {
-                            const float *wrow = Wt + (size_t)sel[r] * D + 8 * c;
+                            const float *wrow = Wt + (size_t)hr * D + 8 * c;
                             const float4 w0 = __ldg(reinterpret_cast<const float4 *>(wrow));
                             const float4 w1 = __ldg(reinterpret_cast<const float4 *>(wrow + 4));
                             float s = v[r];
@@ -363,13 +319,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 // this lane now holds the total of round index jr
                 const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
                                ((lane >> 1) & 1);
-                int myh = 0x7fffffff;
-#pragma unroll
-                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
-                    if (r == lane) myh = sel[r];
-                int rank = 0;
-#pragma unroll
-                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) rank += (sel[r] < myh) ? 1 : 0;
+                const int rank = topk_rank(myh, Hp, lane);
                 const int h_jr = __shfl_sync(0xffffffffu, myh, jr & 31);
                 const int rank_jr = __shfl_sync(0xffffffffu, rank, jr & 31);
                 if ((lane & 1) == 0 && jr < Hp) {
