@@ -250,5 +250,30 @@ def test_bf16_matches_fp32_form_where_selection_agrees(orc):
     assert float((outs[0]["s_mean"][m] - outs[1]["s_mean"][m]).abs().max()) <= 1e-4
     assert float((outs[0]["logZ"][m] - outs[1]["logZ"][m]).abs().max()) <= 1e-3
     # statistics differ only through the near-tie points
-    assert relfro(stats[1]["B"], stats[0]["B"]) <= 1e-3
+    # (R12) the two forms' statistics differ through the ~1.5% near-tie points only
+    assert relfro(stats[1]["B"], stats[0]["B"]) <= 5e-3
     assert abs(stats[1]["scal"][0] - stats[0]["scal"][0]) <= 1e-4 * abs(stats[0]["scal"][0])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_planted_selection_tie(orc, precision):
+    """Two identical dictionary rows give exactly equal scores; when only one of
+    them fits among the H' candidates, the lower index is chosen (both forms)."""
+    from paper_1908_06843_gb300 import Context
+    g = synth.rng(44)
+    H, D = 64, 64
+    Q, _ = np.linalg.qr(g.standard_normal((D, D)))
+    Wt = Q.T.astype(np.float32)         # orthonormal rows: unplanted scores are ~0
+    Wt[40] = Wt[7]                      # duplicate of row 7 at a higher index
+    Y = np.zeros((50, D), np.float32)
+    for n in range(50):                 # strong on 3 distinct rows + the duplicated one
+        Y[n] = 3 * Wt[(n % 5) + 10] + 2 * Wt[(n % 3) + 20] + 1.5 * Wt[7] + 0.01 * g.standard_normal(D)
+    ctx = Context(0, D, H, 3, 2, precision)
+    dev = torch.device("cuda")
+    W = torch.tensor(Wt, device=dev)
+    theta = torch.tensor([0.1, 0.5, 0, 0], dtype=torch.float64, device=dev)
+    P = ctx.params(W, theta)
+    out = ctx.encode(P, torch.tensor(Y, device=dev))
+    sel = out["sel"].cpu().numpy()
+    for n in range(50):
+        assert 7 in sel[n] and 40 not in sel[n], (n, sel[n])
