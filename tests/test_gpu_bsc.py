@@ -263,7 +263,7 @@ def test_planted_selection_tie(orc, precision):
     g = synth.rng(44)
     H, D = 64, 64
     Q, _ = np.linalg.qr(g.standard_normal((D, D)))
-    Wt = Q.T.astype(np.float32)         # orthonormal rows: unplanted scores are ~0
+    Wt = np.ascontiguousarray(Q.T, dtype=np.float32)   # orthonormal rows: unplanted scores ~0
     Wt[40] = Wt[7]                      # duplicate of row 7 at a higher index
     Y = np.zeros((50, D), np.float32)
     for n in range(50):                 # strong on 3 distinct rows + the duplicated one
