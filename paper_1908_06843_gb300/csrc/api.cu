@@ -31,17 +31,18 @@ struct TraceState {
 };
 
 TraceScope::TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream)
-    : c(ctx), s(stream), on(ctx && ctx->trace && ctx->trace->on) {
+    : c(ctx), s(stream), on(ctx && ctx->trace && ctx->trace->on), idx(0) {
     if (!on) return;
     TraceRec r{name, nullptr, nullptr};
     cudaEventCreate(&r.a);
     cudaEventCreate(&r.b);
     cudaEventRecord(r.a, s);
+    idx = c->trace->recs.size();
     c->trace->recs.push_back(r);
 }
 
 TraceScope::~TraceScope() {
-    if (on) cudaEventRecord(c->trace->recs.back().b, s);
+    if (on) cudaEventRecord(c->trace->recs[idx].b, s);
 }
 
 static int num_states(int Hp, int gamma) {
@@ -228,7 +229,10 @@ int prosper_trace_read(prosper_ctx *c, int max, char *names, double *total_ms, i
     std::map<std::string, std::pair<double, int>> acc;
     for (auto &r : c->trace->recs) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
         auto it = acc.find(r.name);

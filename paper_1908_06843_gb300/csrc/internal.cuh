@@ -51,6 +51,7 @@ struct TraceScope {
     prosper_ctx *c;
     cudaStream_t s;
     bool on;
+    size_t idx;   // this scope's record (scopes may nest)
     TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream);
     ~TraceScope();
 };
