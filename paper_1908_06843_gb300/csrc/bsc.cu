@@ -709,16 +709,18 @@ __global__ void k_symmetrize(double *B, int H) {
 // ================================================================ launchers
 int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
     const int H = c->H, D = c->D;
-    TraceScope tr(c, "bsc_prep", s);
-    dim3 gb(16, 16), gg((H + 15) / 16, (H + 15) / 16);
-    k_gram<<<gg, gb, 0, s>>>(W, H, D, c->G);
-    PROSPER_LAUNCH_CHECK();
-    k_rnorm<<<(H + 255) / 256, 256, 0, s>>>(c->G, H, c->rnorm);
-    PROSPER_LAUNCH_CHECK();
-    if (c->Wd) {
-        dim3 tb(32, 8), tg((D + 31) / 32, (H + 31) / 32);
-        k_transpose<<<tg, tb, 0, s>>>(W, H, D, c->Wd);
+    {
+        TraceScope tr(c, "bsc_prep", s);
+        dim3 gb(16, 16), gg((H + 15) / 16, (H + 15) / 16);
+        k_gram<<<gg, gb, 0, s>>>(W, H, D, c->G);
         PROSPER_LAUNCH_CHECK();
+        k_rnorm<<<(H + 255) / 256, 256, 0, s>>>(c->G, H, c->rnorm);
+        PROSPER_LAUNCH_CHECK();
+        if (c->Wd) {
+            dim3 tb(32, 8), tg((D + 31) / 32, (H + 31) / 32);
+            k_transpose<<<tg, tb, 0, s>>>(W, H, D, c->Wd);
+            PROSPER_LAUNCH_CHECK();
+        }
     }
     if (c->Wb) return launch_bsc_bf16_prep(c, W, s);
     return PROSPER_OK;
