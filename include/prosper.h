@@ -141,6 +141,25 @@ int prosper_encode(prosper_ctx *ctx, const prosper_params *p, const float *Y, in
                    int16_t *sel, float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
                    void *stream);
 
+/* BSC encoding without any device allocation (the paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc when they encode -- code
+ * past a fixed start-up phase that must never allocate, a process whose
+ * device memory belongs to a framework's caching allocator, or code that must
+ * not synchronise the device, which cudaMalloc/cudaFree may do).
+ * Same results and output layouts as prosper_encode on a PROSPER_BSC,
+ * PROSPER_FP32 context with these D, H, Hprime, gamma, but no context: the
+ * scratch lives in a fixed ~1.06 MB device array inside the library that
+ * every GPU loading it holds until exit.  Limits: D <= 256, H <= 256,
+ * 1 <= Hprime <= 10, gamma <= Hprime, N <= 4096 per call; larger sizes return
+ * PROSPER_EINVAL.  W (H x D), theta, Y (N x D) and the outputs are device
+ * pointers.  All calls share the array: calls whose GPU work overlaps race,
+ * so issue them on one stream.  The first call on each device looks up the
+ * array's device address; make it before any stream capture. */
+int prosper_encode_noalloc(int D, int H, int Hprime, int gamma, const float *W,
+                           const double *theta, const float *Y, int64_t N, int16_t *sel,
+                           float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
+                           void *stream);
+
 /* Same E-step as prosper_estep with Y and the statistics in HOST memory:
  * Y_host (N x D) is copied to the device in pieces, the statistics are copied
  * back into host arrays At_host (H x D), B_host (H x H), scal_host

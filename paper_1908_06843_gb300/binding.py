@@ -39,6 +39,7 @@ ABI = {
     "prosper_serve_wait": (_I, [_P, ctypes.c_uint64, _I, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "prosper_serve_stop": (_I, [_P]),
+    "prosper_encode_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "prosper_trace_enable": (_I, [_P, _I]),
     "prosper_trace_read": (_I, [_P, _I, _P, _P, _P]),
 }
