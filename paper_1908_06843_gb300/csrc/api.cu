@@ -153,6 +153,11 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     }
     if (gamma < 0 || gamma > Hprime) { set_error("gamma=%d outside [0, Hprime]", gamma); return PROSPER_EINVAL; }
     if (model == PROSPER_GSC && gamma > 3) { set_error("GSC: gamma=%d > 3", gamma); return PROSPER_EINVAL; }
+    if (model == PROSPER_GSC && H > 32) { set_error("GSC: H=%d > 32", H); return PROSPER_EINVAL; }
+    if ((model == PROSPER_GSC || model == PROSPER_MCA) && D > 256) {
+        set_error("MCA/GSC: D=%d > 256", D);
+        return PROSPER_EINVAL;
+    }
     if (precision != PROSPER_FP32 && precision != PROSPER_BF16_RESCORE) {
         set_error("unknown precision %d", precision);
         return PROSPER_EINVAL;
@@ -198,9 +203,12 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     }
     if (model == PROSPER_MCA) ALLOC(c->mca_logW, (size_t)H * D);
     if (model == PROSPER_GSC) {
-        int nsub = 0;
+        int nsub = 0;              // nonempty subsets of at most gamma of the H latents
         double b = 1.0;
-        for (int k = 0; k <= gamma; ++k) { nsub += (int)(b + 0.5); b = b * (H - k) / (k + 1); }
+        for (int k = 0; k <= gamma; ++k) {
+            if (k > 0) nsub += (int)(b + 0.5);
+            b = b * (H - k) / (k + 1);
+        }
         c->gsc_nsub = nsub;
         ALLOC(c->gsc_tab, (size_t)nsub * 8);
     }

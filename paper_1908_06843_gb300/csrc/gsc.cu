@@ -1,7 +1,521 @@
-// gsc.cu -- Gaussian sparse coding (Table 1, spike-and-slab) E-step.
+// gsc.cu -- Gaussian Sparse Coding (Table 1, row GSC: linear superposition,
+// Gaussian noise, spike-and-slab prior s_h = b_h z_h, b_h ~ Bernoulli(pi),
+// z_h ~ N(mu_h, psi_h)) truncated E-step.
+//
+// For an active set b (k = |b| units) the data are Gaussian given b:
+//   y | b ~ N(W_b mu_b, C_b),  C_b = sigma^2 I + W_b Psi_b W_b^T.
+// With M_b = Psi_b^-1 + G_bb / sigma^2 (G = W^T W), Woodbury and the matrix
+// determinant lemma give, relative to the empty state,
+//   l(b) - l(0) = k log(pi/(1-pi)) - (log|Psi_b| + log|M_b|)/2
+//                 - (r_b / sigma^2 - u_b^T M_b^-1 u_b / sigma^4)/2,
+//   u_b = p_b - G_bb mu_b,  r_b = -2 mu_b^T p_b + mu_b^T G_bb mu_b,  p = W^T y,
+// and the slab posterior is N(kappa_b, M_b^-1), kappa_b = M_b^-1 (p_b/sigma^2 + Psi_b^-1 mu_b).
+// log|Psi_b| + log|M_b| and M_b^-1 do not depend on y: k_gsc_table computes
+// them in FP64 for every subset of at most gamma (<= 3) latents once per call
+// (row-a0 constants); the per-state arithmetic is FP32.
+// Preselection score (reading): the singleton log-joint l(e_h).
 #include "internal.cuh"
+#include "topk.cuh"
+
+#include <cmath>
+
 namespace prosper {
-int launch_gsc_prep(prosper_ctx *, const prosper_params *, cudaStream_t) { set_error("GSC not built yet"); return PROSPER_EINVAL; }
-int launch_gsc_estep(prosper_ctx *, const prosper_params *, const float *, int64_t, prosper_stats *,
-                     int16_t *, float *, int16_t *, float *, float *, cudaStream_t) { set_error("GSC not built yet"); return PROSPER_EINVAL; }
+namespace {
+
+constexpr int GW = 8;   // warps per CTA
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kLog2Pi = 1.8378770664093454836;
+constexpr int TAB = 8;  // floats per subset: logdet, Minv 00 01 02 11 12 22, pad
+
+__host__ __device__ inline int64_t binom_small(int n, int k) {
+    if (k < 0 || n < k) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
 }
+// first index of the size-k block (blocks ordered by size, colex inside)
+__host__ __device__ inline int64_t sub_offset(int H, int k) {
+    int64_t o = 0;
+    for (int j = 1; j < k; ++j) o += binom_small(H, j);
+    return o;
+}
+
+// One thread per nonempty subset of at most gamma latents: FP64 Cholesky of
+// M_b, log|Psi_b| + log|M_b| and M_b^-1 (packed upper triangle).
+__global__ void k_gsc_table(const float *__restrict__ G, const float *__restrict__ psi,
+                            const double *__restrict__ theta, int H, int gamma, int nsub,
+                            float *__restrict__ tab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nsub) return;
+    const double sigma = theta[PROSPER_TH_SIGMA];
+    const double is2 = 1.0 / (sigma * sigma);
+    // size class and colex rank
+    int k = 1;
+    int64_t r = t;
+    while (k < gamma && r >= binom_small(H, k)) { r -= binom_small(H, k); ++k; }
+    int b[3] = {0, 0, 0};
+    for (int i = k - 1; i >= 0; --i) {
+        int c = i;
+        while (binom_small(c + 1, i + 1) <= r) ++c;
+        b[i] = c;
+        r -= binom_small(c, i + 1);
+    }
+    double M[3][3], L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double logpsi = 0.0;
+    for (int i = 0; i < k; ++i) {
+        logpsi += log((double)psi[b[i]]);
+        for (int j = 0; j < k; ++j)
+            M[i][j] = (i == j ? 1.0 / (double)psi[b[i]] : 0.0) + is2 * (double)G[(size_t)b[i] * H + b[j]];
+    }
+    double logdetM = 0.0;
+    for (int j = 0; j < k; ++j) {
+        double d = M[j][j];
+        for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
+        d = d > 0.0 ? d : 1e-300;
+        L[j][j] = sqrt(d);
+        logdetM += 2.0 * log(L[j][j]);
+        for (int i = j + 1; i < k; ++i) {
+            double s = M[i][j];
+            for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
+            L[i][j] = s / L[j][j];
+        }
+    }
+    double Mi[3][3];
+    for (int c = 0; c < k; ++c) {          // solve M x = e_c
+        double x[3];
+        for (int i = 0; i < k; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int q = 0; q < i; ++q) s -= L[i][q] * x[q];
+            x[i] = s / L[i][i];
+        }
+        for (int i = k - 1; i >= 0; --i) {
+            double s = x[i];
+            for (int q = i + 1; q < k; ++q) s -= L[q][i] * x[q];
+            x[i] = s / L[i][i];
+        }
+        for (int i = 0; i < k; ++i) Mi[i][c] = x[i];
+    }
+    float *o = tab + (size_t)t * TAB;
+    o[0] = (float)(logpsi + logdetM);
+    o[1] = (float)Mi[0][0];
+    o[2] = k > 1 ? (float)Mi[0][1] : 0.f;
+    o[3] = k > 2 ? (float)Mi[0][2] : 0.f;
+    o[4] = k > 1 ? (float)Mi[1][1] : 0.f;
+    o[5] = k > 2 ? (float)Mi[1][2] : 0.f;
+    o[6] = k > 2 ? (float)Mi[2][2] : 0.f;
+    o[7] = 0.f;
+}
+
+struct GscArgs {
+    const float *W, *Y, *mu, *psi, *G, *tab;
+    const double *theta;
+    int64_t N;
+    int D, H, Hp, gamma, nK;
+    double *At, *B, *scal, *gsc;
+    int16_t *sel_out, *map_out;
+    float *smean_out, *mapp_out, *logz_out;
+};
+
+__device__ __forceinline__ float fast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// per-lane accumulator slots: <b_j> (HP), <s_j> (HP), <s_i s_j> (i <= j)
+template <int HP>
+struct Slots {
+    static constexpr int NB = 0, NS = HP, NP = 2 * HP;
+    static constexpr int N = 2 * HP + HP * (HP + 1) / 2;
+    __device__ static int pair(int i, int j) { return NP + i * HP - i * (i - 1) / 2 + (j - i); }
+};
+
+template <int HP, int DK, bool ENCODE>
+__global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
+    using S = Slots<HP>;
+    extern __shared__ __align__(16) float sm[];
+    const int D = A.D, H = A.H, gamma = A.gamma, nK = A.nK;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *Ws = sm;                                  // H x D
+    float *Gs = Ws + H * D;                          // H x H
+    unsigned *Ks = reinterpret_cast<unsigned *>(Gs + H * H);   // nK canonical masks
+    float *wbase = reinterpret_cast<float *>(Ks + ((nK + 3) & ~3));
+    float *acc = wbase + warp * (S::N * 32 + 64 + 3 * H + H * D);   // per warp
+    unsigned *scratch = reinterpret_cast<unsigned *>(acc + S::N * 32);
+    float *gpart = acc + S::N * 32 + 64;             // 3H
+    float *apart = gpart + 3 * H;                    // H x D
+
+    for (int i = tid; i < H * D; i += GW * 32) Ws[i] = A.W[i];
+    for (int i = tid; i < H * H; i += GW * 32) Gs[i] = A.G[i];
+    if (tid == 0) {   // canonical state masks: by size, then lexicographic
+        int n = 0;
+        for (int k = 0; k <= gamma; ++k) {
+            // enumerate combinations of size k in lexicographic order
+            int idx[HP + 1];
+            for (int i = 0; i < k; ++i) idx[i] = i;
+            for (;;) {
+                unsigned m = 0;
+                for (int i = 0; i < k; ++i) m |= 1u << idx[i];
+                Ks[n++] = m;
+                int i = k - 1;
+                while (i >= 0 && idx[i] == HP - k + i) --i;
+                if (i < 0) break;
+                ++idx[i];
+                for (int j = i + 1; j < k; ++j) idx[j] = idx[j - 1] + 1;
+            }
+        }
+    }
+    if (!ENCODE)
+        for (int i = lane; i < 3 * H + H * D; i += 32) gpart[i] = 0.f;
+    __syncthreads();
+
+    const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
+    const float L2E = 1.4426950408889634f;
+    const float lpi = (float)log(pi / (1.0 - pi));
+    const float is2 = (float)(1.0 / (sigma * sigma));
+    const float is4 = is2 * is2;
+    const double logp00 = H * log(1.0 - pi) - 0.5 * D * (kLog2Pi + log(sigma * sigma));
+    double accF = 0.0, accS1 = 0.0, accYY = 0.0, accN = 0.0;
+
+    const int64_t gw = (int64_t)blockIdx.x * GW + warp, nw = (int64_t)gridDim.x * GW;
+    for (int64_t n = gw; n < A.N; n += nw) {
+        float y[DK];
+#pragma unroll
+        for (int k = 0; k < DK; ++k) {
+            const int d = lane + 32 * k;
+            y[k] = d < D ? A.Y[n * D + d] : 0.f;
+        }
+        float yy = 0.f;
+#pragma unroll
+        for (int k = 0; k < DK; ++k) yy = fmaf(y[k], y[k], yy);
+        yy = wsum(yy);
+        // projections p_h (lane h holds p_h; H <= 32)
+        float ph = 0.f;
+        for (int h = 0; h < H; ++h) {
+            float p = 0.f;
+#pragma unroll
+            for (int k = 0; k < DK; ++k) {
+                const int d = lane + 32 * k;
+                if (d < D) p = fmaf(Ws[h * D + d], y[k], p);
+            }
+            p = wsum(p);
+            if (lane == h) ph = p;
+        }
+        // singleton log-joint (terms common to all h dropped) as the selection score
+        unsigned key[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) key[j] = 0u;
+        if (lane < H) {
+            const float g = Gs[lane * H + lane], m_ = A.mu[lane], ps = A.psi[lane];
+            const float Mh = 1.f / ps + g * is2;
+            const float u = ph - g * m_;
+            const float sc = -0.5f * (logf(ps) + logf(Mh)) - 0.5f * ((-2.f * m_ * ph + m_ * m_ * g) * is2 -
+                                                                      u * u * is4 / Mh);
+            key[0] = score_key(sc);
+        }
+        const int myh = warp_topk(key, A.Hp, lane, scratch);
+        __syncwarp();
+        const int rank = topk_rank(myh, A.Hp, lane);
+        int I[HP];
+        float pI[HP];
+#pragma unroll
+        for (int j = 0; j < HP; ++j) {
+            const unsigned ball = __ballot_sync(0xffffffffu, lane < HP && rank == j);
+            I[j] = __shfl_sync(0xffffffffu, myh, __ffs(ball) - 1);
+            pI[j] = __shfl_sync(0xffffffffu, ph, I[j]);
+        }
+        // ---- states: lane v takes states v, v + 32, ...
+        float lv[8];            // nK <= 1 + 10 + 45 + 120 = 176 states -> <= 6 per lane
+        float m = -INFINITY;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int v = lane + 32 * r;
+            lv[r] = -INFINITY;
+            if (v < nK) {
+                const unsigned mk = Ks[v];
+                const int k = __popc(mk);
+                float l = 0.f;
+                if (k > 0) {
+                    int bl[3] = {0, 0, 0}, bg[3] = {0, 0, 0};
+                    int q = 0;
+#pragma unroll
+                    for (int j = 0; j < HP; ++j)
+                        if (((mk >> j) & 1u) && q < 3) { bl[q] = j; bg[q] = I[j]; ++q; }
+                    int64_t rk = sub_offset(H, k);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        if (i < k) rk += binom_small(bg[i], i + 1);
+                    const float *t = A.tab + rk * TAB;
+                    float mi[3][3];
+                    mi[0][0] = t[1]; mi[0][1] = mi[1][0] = t[2]; mi[0][2] = mi[2][0] = t[3];
+                    mi[1][1] = t[4]; mi[1][2] = mi[2][1] = t[5]; mi[2][2] = t[6];
+                    float p[3], mu[3], u[3], rr = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        float pv = 0.f;
+#pragma unroll
+                        for (int j = 0; j < HP; ++j) pv = (j == bl[i]) ? pI[j] : pv;
+                        p[i] = (i < k) ? pv : 0.f;
+                        mu[i] = (i < k) ? A.mu[bg[i]] : 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        float gm = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            if (i < k && j < k) gm = fmaf(Gs[bg[i] * H + bg[j]], mu[j], gm);
+                        u[i] = p[i] - gm;
+                        rr = fmaf(mu[i], gm - 2.f * p[i], rr);
+                    }
+                    float quad = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            if (i < k && j < k) quad = fmaf(u[i] * mi[i][j], u[j], quad);
+                    l = (float)k * lpi - 0.5f * t[0] - 0.5f * (rr * is2 - quad * is4);
+                }
+                lv[r] = l * L2E;
+                m = fmaxf(m, lv[r]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // ---- posterior moments into lane-private slots
+#pragma unroll 4
+        for (int o = 0; o < S::N; ++o) acc[o * 32 + lane] = 0.f;
+        float Z = 0.f;
+        int best = 0x7fffffff;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int v = lane + 32 * r;
+            if (v >= nK) continue;
+            const unsigned mk = Ks[v];
+            const int k = __popc(mk);
+            const float e = fast_ex2(lv[r] - m);
+            Z += e;
+            const int key_ = (k << 16) + 0xFFFF - (int)(__brev(mk) >> (32 - HP));
+            best = (lv[r] == m) ? min(best, key_) : best;
+            if (k == 0 || e == 0.f) continue;
+            int bl[3] = {0, 0, 0}, bg[3] = {0, 0, 0};
+            int q = 0;
+#pragma unroll
+            for (int j = 0; j < HP; ++j)
+                if (((mk >> j) & 1u) && q < 3) { bl[q] = j; bg[q] = I[j]; ++q; }
+            int64_t rk = sub_offset(H, k);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                if (i < k) rk += binom_small(bg[i], i + 1);
+            const float *t = A.tab + rk * TAB;
+            float mi[3][3];
+            mi[0][0] = t[1]; mi[0][1] = mi[1][0] = t[2]; mi[0][2] = mi[2][0] = t[3];
+            mi[1][1] = t[4]; mi[1][2] = mi[2][1] = t[5]; mi[2][2] = t[6];
+            float w[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float pv = 0.f;
+#pragma unroll
+                for (int j = 0; j < HP; ++j) pv = (j == bl[i]) ? pI[j] : pv;
+                w[i] = (i < k) ? pv * is2 + A.mu[bg[i]] / A.psi[bg[i]] : 0.f;
+            }
+            float kap[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (i < k && j < k) s = fmaf(mi[i][j], w[j], s);
+                kap[i] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (i >= k) break;
+                acc[(S::NB + bl[i]) * 32 + lane] += e;
+                acc[(S::NS + bl[i]) * 32 + lane] += e * kap[i];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (j < i || j >= k) continue;
+                    acc[S::pair(bl[i], bl[j]) * 32 + lane] += e * (mi[i][j] + kap[i] * kap[j]);
+                }
+            }
+        }
+        Z = wsum(Z);
+        best = (int)__reduce_min_sync(0xffffffffu, (unsigned)best);
+        __syncwarp();
+        const float invZ = 1.f / Z;
+        // column sums of the lane-private slots: lane o (and o + 32, ...) owns output o
+        for (int o = lane; o < S::N; o += 32) {
+            float s = 0.f;
+#pragma unroll 8
+            for (int l2 = 0; l2 < 32; ++l2) s += acc[o * 32 + l2];
+            acc[o * 32] = s * invZ;         // slot o, column 0 now holds the normalised value
+        }
+        __syncwarp();
+        const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp00 - (double)yy * 0.5 / (sigma * sigma);
+        if (ENCODE) {
+            if (lane == 0) {
+                if (A.sel_out)
+                    for (int j = 0; j < HP; ++j) A.sel_out[n * HP + j] = (int16_t)I[j];
+                if (A.smean_out)
+                    for (int j = 0; j < HP; ++j) A.smean_out[n * HP + j] = acc[(S::NS + j) * 32];
+                if (A.map_out) {
+                    const unsigned rm = 0xFFFFu - (unsigned)(best & 0xFFFF);
+                    int k = 0;
+                    for (int j = 0; j < HP; ++j)
+                        if (((rm >> (HP - 1 - j)) & 1u) && k < gamma) A.map_out[n * gamma + k++] = (int16_t)I[j];
+                    for (; k < gamma; ++k) A.map_out[n * gamma + k] = (int16_t)-1;
+                }
+                if (A.mapp_out) A.mapp_out[n] = invZ;
+                if (A.logz_out) A.logz_out[n] = (float)logZ;
+            }
+            __syncwarp();
+            continue;
+        }
+        // statistics: B (FP64 atomics on the upper triangle), At and the GSC
+        // sums in warp-private shared partials
+        for (int o = lane; o < HP * (HP + 1) / 2; o += 32) {
+            int i = 0, rem = o;
+            while (rem >= HP - i) { rem -= HP - i; ++i; }
+            const int j = i + rem;
+            const float v = acc[S::pair(i, j) * 32];
+            if (v != 0.f) atomicAdd(A.B + (size_t)I[i < HP ? i : 0] * H + I[j < HP ? j : 0], (double)v);
+        }
+        float s1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < HP; ++j) {
+            const float eb = acc[(S::NB + j) * 32], es = acc[(S::NS + j) * 32];
+            const float ess = acc[S::pair(j, j) * 32];
+            s1 += eb;
+            const int h = I[j];
+            if (lane == 0) {
+                gpart[h] += eb;
+                gpart[H + h] += es;
+                gpart[2 * H + h] += ess;
+            }
+#pragma unroll
+            for (int k = 0; k < DK; ++k) {
+                const int d = lane + 32 * k;
+                if (d < D) apart[h * D + d] = fmaf(es, y[k], apart[h * D + d]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            accF += logZ;
+            accS1 += (double)s1;
+            accYY += (double)yy;
+            accN += 1.0;
+        }
+    }
+    if (ENCODE) return;
+    if (lane == 0) {
+        atomicAdd(A.scal + PROSPER_SC_F, accF);
+        atomicAdd(A.scal + PROSPER_SC_S1, accS1);
+        atomicAdd(A.scal + PROSPER_SC_YY, accYY);
+        atomicAdd(A.scal + PROSPER_SC_N, accN);
+    }
+    __syncthreads();
+    const int stride = S::N * 32 + 64 + 3 * H + H * D;
+    for (int i = tid; i < 3 * H + H * D; i += GW * 32) {
+        float s = 0.f;
+        for (int w = 0; w < GW; ++w) s += wbase[(size_t)w * stride + S::N * 32 + 64 + i];
+        if (s == 0.f) continue;
+        if (i < 3 * H) atomicAdd(A.gsc + i, (double)s);
+        else atomicAdd(A.At + (i - 3 * H), (double)s);
+    }
+}
+
+template <int HP>
+size_t gsc_smem(int D, int H, int nK) {
+    using S = Slots<HP>;
+    size_t f = (size_t)H * D + (size_t)H * H + ((nK + 3) & ~3);
+    f += (size_t)GW * (S::N * 32 + 64 + 3 * H + H * D);
+    return f * sizeof(float);
+}
+
+template <int HP, int DK>
+int gsc_launch2(GscArgs &A, bool enc, int grid, cudaStream_t s) {
+    const size_t smem = gsc_smem<HP>(A.D, A.H, A.nK);
+    if (smem > 227 * 1024) {
+        set_error("GSC: shared memory %zu bytes exceeds the limit (reduce D or H)", smem);
+        return PROSPER_EINVAL;
+    }
+    static size_t attr[2] = {0, 0};
+    if (smem > attr[enc]) {
+        if (enc)
+            PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_gsc_estep<HP, DK, true>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        else
+            PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_gsc_estep<HP, DK, false>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr[enc] = smem;
+    }
+    if (enc) k_gsc_estep<HP, DK, true><<<grid, GW * 32, smem, s>>>(A);
+    else k_gsc_estep<HP, DK, false><<<grid, GW * 32, smem, s>>>(A);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+template <int HP>
+int gsc_launch(GscArgs &A, bool enc, int grid, cudaStream_t s) {
+    const int dk = (A.D + 31) / 32;
+    if (dk <= 1) return gsc_launch2<HP, 1>(A, enc, grid, s);
+    if (dk <= 2) return gsc_launch2<HP, 2>(A, enc, grid, s);
+    if (dk <= 4) return gsc_launch2<HP, 4>(A, enc, grid, s);
+    if (dk <= 8) return gsc_launch2<HP, 8>(A, enc, grid, s);
+    set_error("GSC: D=%d > 256", A.D);
+    return PROSPER_EINVAL;
+}
+
+}  // namespace
+
+int launch_gsc_prep(prosper_ctx *c, const prosper_params *p, cudaStream_t s) {
+    int rc = launch_bsc_prep(c, p->W, s);     // G = W^T W (and 1/||W_h||)
+    if (rc) return rc;
+    TraceScope tr(c, "gsc_table", s);
+    k_gsc_table<<<(c->gsc_nsub + 127) / 128, 128, 0, s>>>(c->G, p->psi, p->theta, c->H, c->gamma,
+                                                          c->gsc_nsub, c->gsc_tab);
+    PROSPER_LAUNCH_CHECK();
+    return PROSPER_OK;
+}
+
+int launch_gsc_estep(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
+                     prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
+                     float *mapp_out, float *logz_out, cudaStream_t s) {
+    if (N <= 0) return PROSPER_OK;
+    if (c->H > 32) {
+        set_error("GSC: H=%d > 32", c->H);
+        return PROSPER_EINVAL;
+    }
+    GscArgs A;
+    A.W = p->W; A.Y = Y; A.mu = p->mu; A.psi = p->psi; A.G = c->G; A.tab = c->gsc_tab;
+    A.theta = p->theta; A.N = N; A.D = c->D; A.H = c->H; A.Hp = c->Hp; A.gamma = c->gamma;
+    A.nK = c->nK;
+    A.At = st ? st->At : nullptr; A.B = st ? st->B : nullptr;
+    A.scal = st ? st->scal : nullptr; A.gsc = st ? st->gsc : nullptr;
+    A.sel_out = sel_out; A.map_out = map_out; A.smean_out = smean_out; A.mapp_out = mapp_out;
+    A.logz_out = logz_out;
+    const bool enc = (st == nullptr);
+    const int64_t warps = (N + 3) / 4;
+    const int grid = (int)std::min<int64_t>((warps + GW - 1) / GW, (int64_t)c->num_sms);
+    TraceScope tr(c, enc ? "gsc_encode" : "gsc_estep", s);
+    switch (c->Hp) {
+        case 1: return gsc_launch<1>(A, enc, grid, s);
+        case 2: return gsc_launch<2>(A, enc, grid, s);
+        case 3: return gsc_launch<3>(A, enc, grid, s);
+        case 4: return gsc_launch<4>(A, enc, grid, s);
+        case 5: return gsc_launch<5>(A, enc, grid, s);
+        case 6: return gsc_launch<6>(A, enc, grid, s);
+        case 7: return gsc_launch<7>(A, enc, grid, s);
+        case 8: return gsc_launch<8>(A, enc, grid, s);
+        case 9: return gsc_launch<9>(A, enc, grid, s);
+        case 10: return gsc_launch<10>(A, enc, grid, s);
+        default: set_error("GSC: unsupported Hprime %d", c->Hp); return PROSPER_EINVAL;
+    }
+}
+
+}  // namespace prosper
