@@ -81,7 +81,8 @@ def test_mca_bars_small_n(orc):
     """MCA bars (D=10x10, H=20, intensity 8, sigma=1), H'=8, gamma=4 (163 states),
     N=1500 (ragged over the persistent warps), rho = 20."""
     d = synth.mca_bars(N=1500, seed=1003)
-    run_model(orc, orc.MCA, d["Y"], d["Wt"], 0.1, 1.0, 8, 4, rho=20.0)
+    # the generating bars are 0 off the bar; MCA needs W > 0 (the M-step keeps W >= 1e-6)
+    run_model(orc, orc.MCA, d["Y"], d["Wt"] + 0.05, 0.1, 1.0, 8, 4, rho=20.0)
     p = synth.init_mca(d["Y"], 20, seed=2003)
     run_model(orc, orc.MCA, d["Y"], p["Wt"], p["pi"], p["sigma"], 8, 4, rho=20.0)
 
