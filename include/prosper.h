@@ -178,6 +178,14 @@ int prosper_estep_host(prosper_ctx *ctx, const prosper_params *p, const float *Y
 int prosper_trace_enable(prosper_ctx *ctx, int on);
 int prosper_trace_read(prosper_ctx *ctx, int max, char *names, double *total_ms, int *launches);
 
+/* Failure detection: synchronise the stream, read and clear the context's
+ * device status word and report what the kernels flagged since the last call:
+ * PROSPER_ENONFINITE (non-finite y^T y of an input point, or an M-step
+ * matrix that is not positive definite), PROSPER_ETIMEOUT (a tensor-core
+ * pipeline wait that gave up after its time limit; the kernel then returned
+ * without touching its outputs further), else PROSPER_OK. */
+int prosper_status(prosper_ctx *ctx, void *stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *prosper_last_error(void);
 

@@ -40,6 +40,7 @@ ABI = {
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "prosper_serve_stop": (_I, [_P]),
     "prosper_encode_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
+    "prosper_status": (_I, [_P, _P]),
     "prosper_trace_enable": (_I, [_P, _I]),
     "prosper_trace_read": (_I, [_P, _I, _P, _P, _P]),
 }
@@ -197,6 +198,10 @@ class Context:
                                            _ptr(At_host), _ptr(B_host), _ptr(scal_host),
                                            _stream(stream)), "prosper_estep_host")
         return dict(At=At_host, B=B_host, scal=scal_host)
+
+    def status(self, stream=None):
+        """Synchronise and report kernel-flagged failures (raises ProsperError)."""
+        _check(self.lib.prosper_status(self.h, _stream(stream)), "prosper_status")
 
     # ------------------------------------------------------------- tracing
     def trace_enable(self, on=True):

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -24,16 +25,17 @@ void set_error(const char *fmt, ...) {
 struct TraceRec {
     const char *name;
     cudaEvent_t a, b;
+    int kernels;
 };
 struct TraceState {
     bool on = false;
     std::vector<TraceRec> recs;
 };
 
-TraceScope::TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream)
+TraceScope::TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream, int kernels)
     : c(ctx), s(stream), on(ctx && ctx->trace && ctx->trace->on), idx(0) {
     if (!on) return;
-    TraceRec r{name, nullptr, nullptr};
+    TraceRec r{name, nullptr, nullptr, kernels};
     cudaEventCreate(&r.a);
     cudaEventCreate(&r.b);
     cudaEventRecord(r.a, s);
@@ -168,6 +170,11 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
         return PROSPER_EINVAL;
     }
     if (max_points <= 0) max_points = 1 << 20;
+    // PROSPER_TEST_TC_NO_COMMIT_MS=<ms> (tests only): the BF16 projection kernel
+    // skips its MMA chain and gives up waiting after <ms>, exercising the
+    // timeout path that prosper_status reports
+    int test_ms = 0;
+    if (const char *e = getenv("PROSPER_TEST_TC_NO_COMMIT_MS")) test_ms = atoi(e);
 
     prosper_ctx *c = new (std::nothrow) prosper_ctx();
     if (!c) { set_error("host allocation failed"); return PROSPER_ENOMEM; }
@@ -175,6 +182,7 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     c->precision = precision;
     c->nK = num_states(Hprime, gamma);
     c->chunk = max_points;
+    c->tc_test_no_commit_ms = (test_ms > 0 && test_ms <= 2000) ? test_ms : 0;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
@@ -222,6 +230,22 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     return PROSPER_OK;
 }
 
+int prosper_status(prosper_ctx *c, void *stream) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned st = 0;
+    PROSPER_CUDA_TRY(cudaMemcpyAsync(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PROSPER_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) {
+        PROSPER_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s));
+        PROSPER_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (st & ST_TC_TIMEOUT) { set_error("a tensor-core pipeline wait gave up"); return PROSPER_ETIMEOUT; }
+    if (st & ST_NONFINITE) { set_error("non-finite value in the input or a result"); return PROSPER_ENONFINITE; }
+    if (st & ST_CHOL_FAIL) { set_error("M-step matrix not positive definite"); return PROSPER_ENONFINITE; }
+    return PROSPER_OK;
+}
+
 int prosper_trace_enable(prosper_ctx *c, int on) {
     if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
     if (!c->trace) c->trace = new TraceState();
@@ -244,8 +268,8 @@ int prosper_trace_read(prosper_ctx *c, int max, char *names, double *total_ms, i
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
         auto it = acc.find(r.name);
-        if (it == acc.end()) { order.push_back(r.name); acc[r.name] = {ms, 1}; }
-        else { it->second.first += ms; it->second.second += 1; }
+        if (it == acc.end()) { order.push_back(r.name); acc[r.name] = {ms, r.kernels}; }
+        else { it->second.first += ms; it->second.second += r.kernels; }
     }
     c->trace->recs.clear();
     int k = 0;

@@ -710,7 +710,7 @@ __global__ void k_symmetrize(double *B, int H) {
 int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
     const int H = c->H, D = c->D;
     {
-        TraceScope tr(c, "bsc_prep", s);
+        TraceScope tr(c, "bsc_prep", s, c->Wd ? 3 : 2);
         dim3 gb(16, 16), gg((H + 15) / 16, (H + 15) / 16);
         k_gram<<<gg, gb, 0, s>>>(W, H, D, c->G);
         PROSPER_LAUNCH_CHECK();

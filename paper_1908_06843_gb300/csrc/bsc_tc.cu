@@ -124,7 +124,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 const uint16_t *__restrict__ Wimg, const float *__restrict__ rnorm, int64_t N,
                 int D, int H, int Hp, uint32_t tmem_cols, int32_t *__restrict__ sel_out,
                 float *__restrict__ selp_out, float2 *__restrict__ yy_out,
-                unsigned *__restrict__ status) {
+                unsigned *__restrict__ status, unsigned long long wait_ns, int test_no_commit) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -211,7 +211,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
         fence_proxy_async();
         __syncthreads();
         // ---- projection tile on the tensor cores
-        if (tid == 0) {
+        if (tid == 0 && !test_no_commit) {
             tc_fence_after();
             const uint32_t ya = smem_u32(Ysm), wa = smem_u32(Wsm);
             for (int kb = 0; kb < nkb; ++kb)
@@ -223,7 +223,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 }
             umma_commit(bar);
         }
-        const bool ok = mbar_wait(bar, phase, kWaitNs);
+        const bool ok = mbar_wait(bar, phase, wait_ns);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
@@ -340,7 +340,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     if (aborted && tid == 0) {
         // give the MMA chain that timed out one more bounded chance to finish
         // before its tensor memory is released
-        mbar_wait(bar, phase ^ 1u, kWaitNs / 2);
+        mbar_wait(bar, phase ^ 1u, wait_ns / 2);
     }
     tc_fence_before();
     __syncthreads();
@@ -398,9 +398,14 @@ int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t
     const int64_t ntiles = (N + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_bf16", s);
+    // fault-injection hook for the failure-detection test: the MMA chain is not
+    // issued, so the bounded wait runs out and the kernel reports a timeout
+    const unsigned long long wait_ns = c->tc_test_no_commit_ms > 0
+                                           ? (unsigned long long)c->tc_test_no_commit_ms * 1000000ull
+                                           : kWaitNs;
     k_bsc_proj_bf16<<<grid, NW * 32, smem, s>>>(Y, W, c->Wb, c->rnorm, N, c->D, c->H, c->Hp, cols,
                                             c->sel, c->selp, reinterpret_cast<float2 *>(c->yy),
-                                            c->d_status);
+                                            c->d_status, wait_ns, c->tc_test_no_commit_ms > 0);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }

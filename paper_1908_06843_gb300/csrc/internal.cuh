@@ -51,8 +51,8 @@ struct TraceScope {
     prosper_ctx *c;
     cudaStream_t s;
     bool on;
-    size_t idx;   // this scope's record (scopes may nest)
-    TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream);
+    size_t idx;   // this scope's record
+    TraceScope(prosper_ctx *ctx, const char *name, cudaStream_t stream, int kernels = 1);
     ~TraceScope();
 };
 
@@ -85,6 +85,7 @@ struct prosper_ctx {
     double *msc = nullptr;    // 16 scalars
 
     unsigned *d_status = nullptr;  // device status word (ST_* bits)
+    int tc_test_no_commit_ms = 0;  // failure-detection test hook (environment, off by default)
 
     // host-staging for prosper_estep_host
     float *h_stage = nullptr;

@@ -201,7 +201,7 @@ int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_par
                  cudaStream_t s) {
     const int H = c->H, D = c->D;
     const double Ntot = (double)N;
-    TraceScope tr(c, "mstep", s);
+    TraceScope tr(c, "mstep", s, c->model == PROSPER_MCA ? 2 : 6);
     if (c->model == PROSPER_MCA) {
         k_mca_w<<<c->num_sms * 4, 256, 0, s>>>(st->mca, p->W, H, D);
         PROSPER_LAUNCH_CHECK();
