@@ -8,3 +8,5 @@ wrapper around it and ``synth`` draws the seeded synthetic workloads.
 from . import binding, synth  # noqa: F401
 from .binding import (BSC, MCA, GSC, FP32, BF16_RESCORE, Context, Params,  # noqa: F401
                       ProsperError, load)
+from .api import (BSC_ET, EM, GSC_ET, MCA_ET, LinearAnnealing, load_params,  # noqa: F401,E402
+                  save_params)

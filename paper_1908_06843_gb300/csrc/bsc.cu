@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
     int I[HP];
     float a[HP], b[HP][HP];
 #pragma unroll
-    for (int j = 0; j < HP; ++j) I[j] = A.sel[nn * SEL_STRIDE + j];
+    for (int j = 0; j < HP; ++j) I[j] = min(max(A.sel[nn * SEL_STRIDE + j], 0), H - 1);   // defensive
 #pragma unroll
     for (int j = 0; j < HP; ++j) {
         float pj = A.selp[nn * SEL_STRIDE + j];
@@ -618,7 +618,7 @@ k_astat(const float *__restrict__ Y, const int32_t *__restrict__ sel, const floa
         __syncthreads();
         for (int i = tid; i < np * Hp; i += 256) {
             int p = i / Hp, j = i - p * Hp;
-            atomicAdd(&cnt[sel[(c0 + p) * SEL_STRIDE + j]], 1);
+            atomicAdd(&cnt[min(max(sel[(c0 + p) * SEL_STRIDE + j], 0), H - 1)], 1);
         }
         // Y slice of the chunk
         if ((D % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
@@ -656,7 +656,7 @@ k_astat(const float *__restrict__ Y, const int32_t *__restrict__ sel, const floa
         __syncthreads();
         for (int i = tid; i < np * Hp; i += 256) {
             int p = i / Hp, j = i - p * Hp;
-            int h = sel[(c0 + p) * SEL_STRIDE + j];
+            int h = min(max(sel[(c0 + p) * SEL_STRIDE + j], 0), H - 1);
             int pos = off[h] + atomicAdd(&fill[h], 1);
             ln[pos] = p;
             lv[pos] = es[(c0 + p) * SEL_STRIDE + j];

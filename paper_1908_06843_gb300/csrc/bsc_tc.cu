@@ -228,6 +228,17 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
             aborted = true;
+            // give every point this CTA still owned a valid (if meaningless)
+            // candidate list so that later kernels stay in bounds
+            for (int64_t t2 = tile; t2 < ntiles; t2 += gridDim.x)
+                for (int i = tid; i < TM * SEL_STRIDE; i += NW * 32) {
+                    const int64_t nn = t2 * TM + i / SEL_STRIDE;
+                    if (nn >= N) continue;
+                    const int j = i % SEL_STRIDE;
+                    sel_out[nn * SEL_STRIDE + j] = j < H ? j : 0;
+                    selp_out[nn * SEL_STRIDE + j] = 0.f;
+                    if (j == 0) yy_out[nn] = make_float2(0.f, 0.f);
+                }
             break;
         }
         tc_fence_after();
