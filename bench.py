@@ -127,9 +127,9 @@ def dist_info():
     return ws, rank, local
 
 
-def make_data(rank):
+def make_data(rank, npts=None):
     from paper_1908_06843_gb300 import synth
-    d = synth.gabor(N=NPTS, seed=1002 + 1000 * rank)
+    d = synth.gabor(N=npts or NPTS, seed=1002 + 1000 * rank)
     return d["Y"], d["Wt"].astype(np.float32)
 
 
@@ -318,6 +318,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--points", type=int, default=NPTS, help="points per GPU (profiling cases)")
+    ap.add_argument("--form", default="both", choices=["both", "bf16_rescore", "fp32"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -336,12 +339,15 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    Y, Wt = make_data(rank)
+    npts = args.points
+    Y, Wt = make_data(rank, npts)
     Yg = torch.tensor(Y, device=dev)
     hbm_peak, bf16_peak, peak_kind = load_peaks()
 
     forms = {}
     for name, prec in [("bf16_rescore", BF16_RESCORE), ("fp32", FP32)]:
+        if args.form not in ("both", name):
+            continue
         try:
             ctx = Context(0, D, H, HP, GAMMA, prec)
         except Exception as e:    # a form that cannot be built is reported, not faked
@@ -353,7 +359,7 @@ def main():
         st = ctx.alloc_stats()
         sampler = ClockSampler(local) if rank == 0 else None
         ms, kern, clocks = bench_form(torch, ctx, P, Yg, st, args.steps, args.warmup, dist, sampler)
-        rl, shares = roofline(kern, args.steps, hbm_peak, peak_kind, NPTS)
+        rl, shares = roofline(kern, args.steps, hbm_peak, peak_kind, npts)
         launches = sum(v[1] for v in kern.values()) / args.steps
         # M-step and encode (timed separately; not part of the E-step metric)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -361,7 +367,7 @@ def main():
         thsave = theta.clone()
         e0.record()
         for _ in range(3):
-            ctx.mstep(st, NPTS, P)
+            ctx.mstep(st, npts, P)
             W.copy_(Wsave)
             theta.copy_(thsave)
         e1.record()
@@ -375,32 +381,35 @@ def main():
         torch.cuda.synchronize()
         encode_ms = e0.elapsed_time(e1) / 5
         # end to end through the C ABI with host buffers (pinned), copies inside
-        Yh = torch.from_numpy(Y).pin_memory()
-        At_h = np.zeros((H, D))
-        B_h = np.zeros((H, H))
-        sc_h = np.zeros(8)
-        for _ in range(2):
-            ctx.estep_host(P, Yh, At_h, B_h, sc_h)
-        e2e_steps = max(3, min(args.steps, 20))
-        if dist is not None:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            ctx.estep_host(P, Yh, At_h, B_h, sc_h)
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e = None
+        if not args.no_e2e:
+            Yh = torch.from_numpy(Y).pin_memory()
+            At_h = np.zeros((H, D))
+            B_h = np.zeros((H, H))
+            sc_h = np.zeros(8)
+            for _ in range(2):
+                ctx.estep_host(P, Yh, At_h, B_h, sc_h)
+            e2e_steps = max(3, min(args.steps, 20))
+            if dist is not None:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                ctx.estep_host(P, Yh, At_h, B_h, sc_h)
+            e2e_s = time.perf_counter() - t0
+            if dist is not None:
+                t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                e2e_s = float(t.item())
+            e2e = {"value": npts * ws * e2e_steps / e2e_s, "unit": "points/s",
+                   "h2d_bytes_per_step": npts * D * 4,
+                   "d2h_bytes_per_step": (H * D + H * H + 8) * 8}
         forms[name] = {
-            "value": NPTS * ws * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "value": npts * ws * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
             "roofline": rl, "kernels": shares, "gpu_launches_per_step": launches,
             "clocks": clocks, "mstep_ms": mstep_ms, "encode_ms": encode_ms,
             "em_iteration_ms": ms / args.steps + mstep_ms,
-            "e2e": {"value": NPTS * ws * e2e_steps / e2e_s, "unit": "points/s",
-                    "h2d_bytes_per_step": NPTS * D * 4,
-                    "d2h_bytes_per_step": (H * D + H * H + 8) * 8},
-            "F_per_point": float(st["scal"][0].item()) / NPTS,
+            "e2e": e2e,
+            "F_per_point": float(st["scal"][0].item()) / npts,
         }
         ctx.close()
         del P, st
@@ -427,7 +436,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16+f32" if head_name == "bf16_rescore" else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": head_name, "global_points": NPTS * ws,
+        "config": {"workload": WORKLOAD, "form": head_name, "global_points": npts * ws,
                    "l2": "inputs larger than L2 (Y 204.8 MB per GPU), no flush",
                    "parallelism": f"weak x{ws}, no data-path collective"},
         "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"],
