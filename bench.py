@@ -225,6 +225,27 @@ def bench_form(torch, ctx, P, Yg, st, steps, warmup, dist, sampler):
     return ms, kern, clocks
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per point of `kernel` from profiles/traffic.txt, or None when
+    the kernel's sources changed since that ncu capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, bpp, files, digest = line.split()
+        if name != kernel:
+            continue
+        m = hashlib.sha256()
+        for f in files.split(","):
+            with open(os.path.join(ROOT, "paper_1908_06843_gb300", "csrc", f), "rb") as fh:
+                m.update(fh.read())
+        return float(bpp) if m.hexdigest()[:16] == digest else None
+    return None
+
+
 def roofline(kern, steps, hbm_peak, peak_kind, npts):
     per = {k: v[0] / steps for k, v in kern.items()}
     total = sum(per.values())
@@ -242,7 +263,13 @@ def roofline(kern, steps, hbm_peak, peak_kind, npts):
         rl = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
               "frac": achieved / hbm_peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     rl["kernel"] = top
-    rl["traffic"] = None
+    bpp = measured_traffic(top)
+    if bpp is not None:
+        rl["traffic"] = bpp * npts
+        rl["traffic_unit"] = "bytes per launch (ncu dram read+write, 150k-point capture scaled per point)"
+        rl["algorithmic_bytes"] = (4 * D + 136) * npts if top.startswith("bsc_proj") else None
+    else:
+        rl["traffic"] = None
     shares = {k: {"ms_per_step": v, "share": v / total,
                   "launches_per_step": kern[k][1] / steps} for k, v in per.items()}
     return rl, shares
