@@ -46,7 +46,7 @@ WORKLOAD = "BSC Gabor patches D=256 H=256 H'=10 gamma=5 (638 states) N=200000/GP
 SMS, LANES, FMAX_GHZ = 152, 128, 2.07
 ALU_PEAK_TOPS = SMS * LANES * FMAX_GHZ * 1e9 / 1e12   # 40.28 T lane-ops/s
 
-# Algorithmic work per data point of each kernel ("Kernels").
+# Algorithmic work per data point of each kernel.
 KERNEL_WORK = {
     # kernel: (bound, units per point, unit)
     "bsc_proj_f32": ("alu", D * H, "lane-op"),            # W^T y: D*H FMA
