@@ -183,6 +183,7 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     c->nK = num_states(Hprime, gamma);
     c->chunk = max_points;
     c->tc_test_no_commit_ms = (test_ms > 0 && test_ms <= 2000) ? test_ms : 0;
+    if (const char *e = getenv("PROSPER_ASTAT_SIMT")) c->astat_simt = atoi(e) != 0;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {

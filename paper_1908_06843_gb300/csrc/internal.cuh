@@ -86,6 +86,7 @@ struct prosper_ctx {
 
     unsigned *d_status = nullptr;  // device status word (ST_* bits)
     int tc_test_no_commit_ms = 0;  // failure-detection test hook (environment, off by default)
+    int astat_simt = 0;            // 1: use the SIMT kernel for sum y<s>^T (PROSPER_ASTAT_SIMT=1)
 
     // host-staging for prosper_estep_host
     float *h_stage = nullptr;
@@ -111,6 +112,8 @@ int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_
                       prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
                       float *mapp_out, float *logz_out, cudaStream_t s);
 int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s);
+int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s);
+bool astat_tc_ok(int D, int H);
 int launch_symmetrize(prosper_ctx *c, double *B, cudaStream_t s);
 
 int launch_mca_prep(prosper_ctx *c, const float *W, cudaStream_t s);

@@ -277,3 +277,27 @@ def test_planted_selection_tie(orc, precision):
     sel = out["sel"].cpu().numpy()
     for n in range(50):
         assert 7 in sel[n] and 40 not in sel[n], (n, sel[n])
+
+
+def test_tensor_core_and_simt_astat_agree(orc):
+    """sum_n <s>_n y_n^T from the tcgen05 kernel (BF16 hi/lo split products)
+    equals the SIMT FP32 kernel's to well inside the 1e-5 aggregate tolerance."""
+    import os
+    from paper_1908_06843_gb300 import Context
+    d = synth.gabor(N=20000, seed=1002)
+    dev = torch.device("cuda")
+    W = torch.tensor(d["Wt"].astype(np.float32), device=dev)
+    theta = torch.tensor([4 / 256, 0.2, 0, 0], dtype=torch.float64, device=dev)
+    Y = torch.tensor(d["Y"], device=dev)
+    out = []
+    for simt in ("0", "1"):
+        os.environ["PROSPER_ASTAT_SIMT"] = simt
+        try:
+            ctx = Context(0, 256, 256, 10, 5, 0)
+        finally:
+            del os.environ["PROSPER_ASTAT_SIMT"]
+        st = ctx.alloc_stats()
+        ctx.estep(ctx.params(W, theta), Y, st)
+        torch.cuda.synchronize()
+        out.append(st["At"].cpu().numpy())
+    assert relfro(out[0], out[1]) <= 1e-6, relfro(out[0], out[1])
