@@ -71,47 +71,88 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
+    // E starts zeroed once; afterwards every point column is cleared by the
+    // thread that owns it (thread t < 64 writes only column t)
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(Ehi);
+        const int nz = 2 * Hpad * 128 / 16;
+        for (int i = tid; i < nz; i += AT_NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    int prev_h[PROSPER_MAX_HPRIME];
+#pragma unroll
+    for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) prev_h[j] = -1;
+
+    // Y of a tile in registers: work item w = (4 consecutive d, 8-point chunk c)
+    const int items = (D / 4) * (AT_T / 8);            // <= 512 for D <= 256
+    float4 yv[2][8];
+    auto prefetch = [&](int64_t t) {
+        const int64_t base = t * AT_T;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int w = tid + AT_NT * r;
+            const int d4 = (w % (D / 4)) * 4, c = w / (D / 4);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t n = base + 8 * c + i;
+                yv[r][i] = (w < items && n < N) ? __ldg(reinterpret_cast<const float4 *>(Y + n * D + d4))
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+
     uint32_t phase = 0;
     bool aborted = false;
     int done_tiles = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) prefetch(tile);
+    __syncthreads();
+    for (; tile < ntiles; tile += gridDim.x) {
         const int64_t n0 = tile * AT_T;
-        // ---- E operand: zero, then scatter the tile's (h, <s_h>) pairs
-        {
-            uint4 *z = reinterpret_cast<uint4 *>(Ehi);
-            const int nz = 2 * Hpad * 128 / 16;        // Ehi and Elo are contiguous
-            for (int i = tid; i < nz; i += AT_NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
-        }
-        __syncthreads();
+        // ---- E operand: clear this column's previous entries, write the new ones
         if (tid < AT_T) {
+#pragma unroll
+            for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
+                if (prev_h[j] >= 0) {
+                    const uint32_t off = kmaj_off(prev_h[j], tid);
+                    *reinterpret_cast<uint16_t *>(Ehi + off) = 0;
+                    *reinterpret_cast<uint16_t *>(Elo + off) = 0;
+                    prev_h[j] = -1;
+                }
             const int64_t n = n0 + tid;
             if (n < N) {
-                for (int j = 0; j < Hp; ++j) {
+#pragma unroll
+                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+                    if (j >= Hp) break;
                     const int h = min(max(sel[n * SEL_STRIDE + j], 0), H - 1);
                     __nv_bfloat16 hi, lo;
                     split_bf16(es[n * SEL_STRIDE + j], hi, lo);
                     const uint32_t off = kmaj_off(h, tid);
                     *reinterpret_cast<__nv_bfloat16 *>(Ehi + off) = hi;
                     *reinterpret_cast<__nv_bfloat16 *>(Elo + off) = lo;
+                    prev_h[j] = h;
                 }
             }
         }
-        // ---- Y operand, transposed: thread d packs 8 consecutive points per 16-byte chunk
-        for (int d = tid; d < D; d += AT_NT) {
+        // ---- Y operand, transposed (points contiguous), hi and lo parts
 #pragma unroll
-            for (int c = 0; c < AT_T / 8; ++c) {
+        for (int r = 0; r < 2; ++r) {
+            const int w = tid + AT_NT * r;
+            if (w >= items) continue;
+            const int d4 = (w % (D / 4)) * 4, c = w / (D / 4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
                 uint32_t ph[4], pl[4];
 #pragma unroll
                 for (int i = 0; i < 8; i += 2) {
-                    const int64_t na = n0 + 8 * c + i, nb = na + 1;
-                    const float a = na < N ? __ldg(Y + na * D + d) : 0.f;
-                    const float b = nb < N ? __ldg(Y + nb * D + d) : 0.f;
+                    const float a = e == 0 ? yv[r][i].x : e == 1 ? yv[r][i].y : e == 2 ? yv[r][i].z : yv[r][i].w;
+                    const float b = e == 0 ? yv[r][i + 1].x : e == 1 ? yv[r][i + 1].y : e == 2 ? yv[r][i + 1].z : yv[r][i + 1].w;
                     __nv_bfloat16 ah, al, bh, bl;
                     split_bf16(a, ah, al);
                     split_bf16(b, bh, bl);
                     ph[i >> 1] = (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
                     pl[i >> 1] = (uint32_t)__bfloat16_as_ushort(al) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
                 }
+                const int d = d4 + e;
                 const uint32_t off = (uint32_t)(d * 128 + ((c ^ (d & 7)) << 4));
                 *reinterpret_cast<uint4 *>(Yhi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
                 *reinterpret_cast<uint4 *>(Ylo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
@@ -135,6 +176,8 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
             }
             umma_commit(bar);
         }
+        // the next tile's data travel while the tensor cores work
+        if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
         const bool ok = mbar_wait(bar, phase, kAtWaitNs);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
