@@ -100,14 +100,29 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
         }
     };
 
+    // the tile's candidate lists and posterior means (thread t < 64: point t)
+    int sh[PROSPER_MAX_HPRIME];
+    float sv[PROSPER_MAX_HPRIME];
+    auto prefetch_e = [&](int64_t t) {
+        const int64_t n = t * AT_T + tid;
+#pragma unroll
+        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+            const bool ok = tid < AT_T && n < N && j < Hp;
+            sh[j] = ok ? min(max(__ldg(sel + n * SEL_STRIDE + j), 0), H - 1) : -1;
+            sv[j] = ok ? __ldg(es + n * SEL_STRIDE + j) : 0.f;
+        }
+    };
+
     uint32_t phase = 0;
     bool aborted = false;
     int done_tiles = 0;
     int64_t tile = blockIdx.x;
-    if (tile < ntiles) prefetch(tile);
+    if (tile < ntiles) {
+        prefetch(tile);
+        prefetch_e(tile);
+    }
     __syncthreads();
     for (; tile < ntiles; tile += gridDim.x) {
-        const int64_t n0 = tile * AT_T;
         // ---- E operand: clear this column's previous entries, write the new ones
         if (tid < AT_T) {
 #pragma unroll
@@ -118,19 +133,16 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
                     *reinterpret_cast<uint16_t *>(Elo + off) = 0;
                     prev_h[j] = -1;
                 }
-            const int64_t n = n0 + tid;
-            if (n < N) {
 #pragma unroll
-                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
-                    if (j >= Hp) break;
-                    const int h = min(max(sel[n * SEL_STRIDE + j], 0), H - 1);
-                    __nv_bfloat16 hi, lo;
-                    split_bf16(es[n * SEL_STRIDE + j], hi, lo);
-                    const uint32_t off = kmaj_off(h, tid);
-                    *reinterpret_cast<__nv_bfloat16 *>(Ehi + off) = hi;
-                    *reinterpret_cast<__nv_bfloat16 *>(Elo + off) = lo;
-                    prev_h[j] = h;
-                }
+            for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+                const int h = sh[j];
+                if (h < 0) continue;
+                __nv_bfloat16 hi, lo;
+                split_bf16(sv[j], hi, lo);
+                const uint32_t off = kmaj_off(h, tid);
+                *reinterpret_cast<__nv_bfloat16 *>(Ehi + off) = hi;
+                *reinterpret_cast<__nv_bfloat16 *>(Elo + off) = lo;
+                prev_h[j] = h;
             }
         }
         // ---- Y operand, transposed (points contiguous), hi and lo parts
@@ -177,7 +189,10 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
             umma_commit(bar);
         }
         // the next tile's data travel while the tensor cores work
-        if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+        if (tile + gridDim.x < ntiles) {
+            prefetch(tile + gridDim.x);
+            prefetch_e(tile + gridDim.x);
+        }
         const bool ok = mbar_wait(bar, phase, kAtWaitNs);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
