@@ -208,6 +208,7 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
         ALLOC(c->sel, ch * SEL_STRIDE);
         ALLOC(c->selp, ch * SEL_STRIDE);
         ALLOC(c->es, ch * SEL_STRIDE);
+        if (astat_tc_ok(D, H)) ALLOC(c->apart, (size_t)c->num_sms * H * D);
         ALLOC(c->yy, ch * 2);
     }
     if (model == PROSPER_MCA) ALLOC(c->mca_logW, (size_t)H * D);
@@ -294,7 +295,7 @@ int prosper_destroy(prosper_ctx *c) {
     cudaFree(c->d_hstats);
     cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
     cudaFree(c->mca_logW); cudaFree(c->gsc_tab);
-    cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es);
+    cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es); cudaFree(c->apart);
     cudaFree(c->mB); cudaFree(c->mX); cudaFree(c->msc); cudaFree(c->d_status);
     cudaFree(c->d_stage);
     if (c->h_stage) cudaFreeHost(c->h_stage);

@@ -40,7 +40,7 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
 
 __global__ void __launch_bounds__(AT_NT, 1)
 k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const float *__restrict__ es,
-           int64_t N, int D, int H, int Hp, int halves, uint32_t tmem_cols, double *__restrict__ At,
+           int64_t N, int D, int H, int Hp, int halves, uint32_t tmem_cols, float *__restrict__ part,
            unsigned *__restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t mbar;
@@ -203,20 +203,27 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
         tc_fence_after();
         ++done_tiles;
     }
-    // ---- epilogue: tensor memory -> FP64 statistic (once per CTA)
-    if (!aborted && done_tiles > 0) {
+    // ---- epilogue: this CTA's FP32 partial of A^T to global memory (plain
+    //      stores; k_reduce_parts sums the partials in FP64 in a fixed order)
+    if (!aborted) {
         const int q = warp & 3;
         const int h_in = q * 32 + lane;
         const int cb = (warp < 4) ? 0 : D / 2, ce = (warp < 4) ? D / 2 : D;
+        float *mine = part + (size_t)blockIdx.x * H * D;
         for (int hf = 0; hf < halves; ++hf) {
             const int h = hf * 128 + h_in;
             for (int c0 = cb; c0 < ce; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * D + c0), v);
-                if (h < H) {
+                if (done_tiles > 0) {
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * D + c0), v);
+                } else {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k)
-                        if (v[k] != 0.f) atomicAdd(At + (size_t)h * D + c0 + k, (double)v[k]);
+                    for (int k = 0; k < 16; ++k) v[k] = 0.f;
+                }
+                if (h < H) {
+                    float4 *dst = reinterpret_cast<float4 *>(mine + (size_t)h * D + c0);
+#pragma unroll
+                    for (int k = 0; k < 16; k += 4) dst[k / 4] = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
                 }
             }
         }
@@ -228,6 +235,18 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
                      : "memory");
+    }
+}
+
+// At += sum over the per-CTA partials, in FP64 and in CTA order
+__global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int64_t HD,
+                               double *__restrict__ At) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < HD;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+#pragma unroll 8
+        for (int p = 0; p < nparts; ++p) s += (double)__ldg(part + (size_t)p * HD + i);
+        At[i] += s;
     }
 }
 
@@ -250,9 +269,13 @@ int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaS
     while ((int)cols < halves * D) cols <<= 1;
     const int64_t ntiles = (N + AT_T - 1) / AT_T;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
-    TraceScope tr(c, "astat_tc", s);
-    k_astat_tc<<<grid, AT_NT, smem, s>>>(Y, c->sel, c->es, N, D, H, c->Hp, halves, cols, At,
+    TraceScope tr(c, "astat_tc", s, 2);
+    k_astat_tc<<<grid, AT_NT, smem, s>>>(Y, c->sel, c->es, N, D, H, c->Hp, halves, cols, c->apart,
                                          c->d_status);
+    PROSPER_LAUNCH_CHECK();
+    const int64_t HD = (int64_t)H * D;
+    k_reduce_parts<<<(int)std::min<int64_t>((HD + 255) / 256, 4 * c->num_sms), 256, 0, s>>>(
+        c->apart, grid, HD, At);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }

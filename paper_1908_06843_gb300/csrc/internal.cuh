@@ -78,6 +78,7 @@ struct prosper_ctx {
     float *selp = nullptr;    // chunk x SEL_STRIDE FP32 projections of the selected latents
     float *yy = nullptr;      // chunk x 2: y^T y as an unevaluated sum hi + lo
     float *es = nullptr;      // chunk x SEL_STRIDE posterior means <s> of the selected latents
+    float *apart = nullptr;   // num_sms x H x D FP32 partials of sum y<s>^T (tensor-core path)
 
     // M-step workspace (FP64)
     double *mB = nullptr;     // H x H
