@@ -195,12 +195,15 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     const size_t ch = (size_t)c->chunk;
 #define ALLOC(ptr, n) do { if (!rc) rc = dev_alloc(&(ptr), (n)); } while (0)
     ALLOC(c->d_status, 1);
-    ALLOC(c->msc, 16);
     if (model == PROSPER_BSC || model == PROSPER_GSC) {
         ALLOC(c->G, (size_t)H * H);
         ALLOC(c->rnorm, (size_t)H);
-        ALLOC(c->mB, (size_t)H * H);
-        ALLOC(c->mX, (size_t)H * D);
+        const size_t Hq = (size_t)mstep_hq(H);
+        ALLOC(c->mB, Hq * Hq);
+        ALLOC(c->mX, Hq * D);
+        ALLOC(c->mI, Hq * Hq);
+        ALLOC(c->mW, (size_t)H * D);
+        ALLOC(c->mpart, (size_t)mstep_nparts(H, D));
     }
     if (model == PROSPER_BSC) {
         if (precision == PROSPER_FP32) ALLOC(c->Wd, (size_t)D * H);
@@ -296,7 +299,7 @@ int prosper_destroy(prosper_ctx *c) {
     cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
     cudaFree(c->mca_logW); cudaFree(c->gsc_tab);
     cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es); cudaFree(c->apart);
-    cudaFree(c->mB); cudaFree(c->mX); cudaFree(c->msc); cudaFree(c->d_status);
+    cudaFree(c->mB); cudaFree(c->mX); cudaFree(c->mI); cudaFree(c->mW); cudaFree(c->mpart); cudaFree(c->d_status);
     cudaFree(c->d_stage);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     delete c;

@@ -81,9 +81,11 @@ struct prosper_ctx {
     float *apart = nullptr;   // num_sms x H x D FP32 partials of sum y<s>^T (tensor-core path)
 
     // M-step workspace (FP64)
-    double *mB = nullptr;     // H x H
-    double *mX = nullptr;     // H x D
-    double *msc = nullptr;    // 16 scalars
+    double *mB = nullptr;     // Hq x Hq (Hq = H rounded up to 32): B, then its Cholesky factor
+    double *mX = nullptr;     // Hq x D: At, then L^-1 At
+    double *mI = nullptr;     // Hq x Hq: identity, then L^-1
+    double *mW = nullptr;     // H x D: the new W^T in FP64
+    double *mpart = nullptr;  // per-CTA partials of tr(W^T A) and tr(W^T W B)
 
     unsigned *d_status = nullptr;  // device status word (ST_* bits)
     int tc_test_no_commit_ms = 0;  // failure-detection test hook (environment, off by default)
@@ -127,6 +129,8 @@ int launch_gsc_estep(prosper_ctx *c, const prosper_params *p, const float *Y, in
                      prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
                      float *mapp_out, float *logz_out, cudaStream_t s);
 
+int mstep_hq(int H);
+int mstep_nparts(int H, int D);
 int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_params *p,
                  cudaStream_t s);
 

@@ -129,6 +129,46 @@ def test_mstep_matches_oracle(orc):
     assert abs(th[0] - pi2) <= 1e-9 and abs(th[1] - s2) <= 1e-7 * s2
 
 
+def _synthetic_stats(H, D, N, seed, inactive=()):
+    """Sufficient statistics with the structure of a truncated E-step: fractional
+    posterior means <s> (sparse), B = sum <s><s>^T + diag(sum <s>(1-<s>)),
+    At = sum <s> y^T; the units in `inactive` are never active."""
+    rng = np.random.default_rng(seed)
+    S = rng.random((N, H)) * (rng.random((N, H)) < 0.04)
+    S[:, list(inactive)] = 0.0
+    Y = rng.standard_normal((N, D))
+    B = S.T @ S + np.diag((S * (1 - S)).sum(0))
+    At = S.T @ Y
+    scal = np.zeros(8)
+    scal[1], scal[2], scal[3] = S.sum(), (Y * Y).sum(), N
+    return {"At": At, "B": B, "scal": scal, "gsc": None, "mca": None}
+
+
+@pytest.mark.parametrize("H,D,inactive", [(256, 256, ()), (256, 256, (0, 77, 255)),
+                                          (70, 100, (5,)), (33, 40, ()), (16, 25, (15,))])
+def test_mstep_blocked_solve_matches_oracle(orc, H, D, inactive):
+    """The blocked FP64 M-step at the Gabor size (H=D=256) and at ragged orders
+    (H not a multiple of the 32-block, D not a multiple of the tiles), with
+    never-active units, against the oracle's M-step on the same statistics."""
+    from paper_1908_06843_gb300 import Context
+    N = 6000
+    st = _synthetic_stats(H, D, N, seed=H + D, inactive=inactive)
+    rng = np.random.default_rng(7)
+    Wt0 = rng.standard_normal((H, D)).astype(np.float32)
+    ctx, W, theta, _, P = _setup((0, D, H, min(H, 8), 3, 0), np.zeros((1, D)), Wt0, 0.1, 1.0)
+    W2, pi2, s2, _, _ = orc.mstep(orc.BSC, N, st, Wt0.astype(np.float64), 0.1, 1.0)
+    stg = {k: (None if v is None else torch.tensor(v, device="cuda")) for k, v in st.items()}
+    ctx.mstep(stg, N, P)
+    torch.cuda.synchronize()
+    ctx.status()
+    Wg = W.cpu().numpy()
+    assert relfro(Wg, W2) <= 1e-6, relfro(Wg, W2)
+    for h in inactive:       # a never-active unit keeps its W_h bit for bit
+        assert np.array_equal(Wg[h], Wt0[h])
+    th = theta.cpu().numpy()
+    assert abs(th[0] - pi2) <= 1e-9 and abs(th[1] - s2) <= 1e-7 * s2
+
+
 def test_em_trajectory_on_bars(orc):
     """20 EM iterations on the GPU; each step checked one at a time against the
     oracle fed the GPU's parameters; the bars are recovered."""
