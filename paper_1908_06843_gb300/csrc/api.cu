@@ -202,6 +202,9 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
         ALLOC(c->mB, Hq * Hq);
         ALLOC(c->mX, Hq * D);
         ALLOC(c->mI, Hq * Hq);
+        ALLOC(c->mP, Hq * 32);
+        ALLOC(c->mY, Hq * D);
+        ALLOC(c->mZ, Hq * Hq);
         ALLOC(c->mW, (size_t)H * D);
         ALLOC(c->mpart, (size_t)mstep_nparts(H, D));
     }
@@ -299,7 +302,7 @@ int prosper_destroy(prosper_ctx *c) {
     cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
     cudaFree(c->mca_logW); cudaFree(c->gsc_tab);
     cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es); cudaFree(c->apart);
-    cudaFree(c->mB); cudaFree(c->mX); cudaFree(c->mI); cudaFree(c->mW); cudaFree(c->mpart); cudaFree(c->d_status);
+    cudaFree(c->mB); cudaFree(c->mX); cudaFree(c->mI); cudaFree(c->mP); cudaFree(c->mY); cudaFree(c->mZ); cudaFree(c->mW); cudaFree(c->mpart); cudaFree(c->d_status);
     cudaFree(c->d_stage);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     delete c;

@@ -81,9 +81,12 @@ struct prosper_ctx {
     float *apart = nullptr;   // num_sms x H x D FP32 partials of sum y<s>^T (tensor-core path)
 
     // M-step workspace (FP64)
-    double *mB = nullptr;     // Hq x Hq (Hq = H rounded up to 32): B, then its Cholesky factor
-    double *mX = nullptr;     // Hq x D: At, then L^-1 At
-    double *mI = nullptr;     // Hq x Hq: identity, then L^-1
+    double *mB = nullptr;     // Hq x Hq (Hq = H rounded up to 32): B and its trailing updates
+    double *mX = nullptr;     // Hq x D: At and its trailing updates
+    double *mI = nullptr;     // Hq x Hq: identity and its trailing updates
+    double *mP = nullptr;     // Hq x 32: the current panel of the Cholesky factor
+    double *mY = nullptr;     // Hq x D: L^-1 At
+    double *mZ = nullptr;     // Hq x Hq: L^-1
     double *mW = nullptr;     // H x D: the new W^T in FP64
     double *mpart = nullptr;  // per-CTA partials of tr(W^T A) and tr(W^T W B)
 
