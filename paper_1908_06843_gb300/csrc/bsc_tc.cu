@@ -10,9 +10,12 @@
 // resident in shared memory for the whole persistent CTA.  The accumulator
 // tile (128 lanes x H columns, FP32) is read back with tcgen05.ld, staged in
 // shared memory 64 points at a time, and every warp takes the top-H' of its
-// points exactly as the FP32 path does (ties to the lower h).  The H' selected
-// projections are then recomputed in FP32 from the FP32 Y and W, so BF16 only
-// decides which latents are candidates.
+// points.  The ranking key is the score rounded down to 15 mantissa bits with
+// 255 - h in the low byte (ties, including the ones the rounding makes, go to
+// the lower h); the rounding is far below the BF16 error of the score itself.
+// Each lane sorts its 8 keys, then H' rounds of a warp maximum pop the winners.
+// The H' selected projections are then recomputed in FP32 from the FP32 Y and
+// W, so BF16 only decides which latents are candidates.
 //
 // Shared memory (1024-byte aligned, K-major, 128-byte swizzle, 8-row core groups):
 //   W  : D/64 K-blocks, each H rows x 128 B    (H*D*2 bytes, resident)
@@ -38,6 +41,18 @@ __device__ __forceinline__ int pidx(int row, int col, int H) {
     return row * H + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
 }
 
+// descending sort of 8 keys: Batcher's odd-even merge network (19 comparators)
+__device__ __forceinline__ void sort8_desc(unsigned (&k)[8]) {
+#define PROSPER_CE(i, j) { const unsigned a = max(k[i], k[j]), b = min(k[i], k[j]); k[i] = a; k[j] = b; }
+    PROSPER_CE(0, 1) PROSPER_CE(2, 3) PROSPER_CE(4, 5) PROSPER_CE(6, 7)
+    PROSPER_CE(0, 2) PROSPER_CE(1, 3) PROSPER_CE(4, 6) PROSPER_CE(5, 7)
+    PROSPER_CE(1, 2) PROSPER_CE(5, 6)
+    PROSPER_CE(0, 4) PROSPER_CE(1, 5) PROSPER_CE(2, 6) PROSPER_CE(3, 7)
+    PROSPER_CE(2, 4) PROSPER_CE(3, 5)
+    PROSPER_CE(1, 2) PROSPER_CE(3, 4) PROSPER_CE(5, 6)
+#undef PROSPER_CE
+}
+
 // byte offset of the 16-byte chunk c (8 BF16 values, d = 8c .. 8c+7) of row r in a
 // K-major 128-byte-swizzled operand with `rows` rows per 64-wide K-block
 __device__ __forceinline__ uint32_t opnd_off(int r, int c, int rows) {
@@ -54,7 +69,6 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_slot;
-    __shared__ unsigned topk_scratch[NW][64];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *sbase = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const size_t wbytes = (size_t)H * D * 2;
@@ -101,37 +115,55 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     bool aborted = false;
     for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
         const int64_t n0 = tile * TM;
-        // ---- Y tile -> BF16 operand; exact y^T y on the way
-        for (int r = warp; r < TM; r += NW) {
-            const int64_t n = n0 + r;
-            float sq = 0.f;
-            for (int c = lane; c < nchunk; c += 32) {
-                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-                if (n < N) {
+        // ---- Y tile -> BF16 operand; exact y^T y on the way.  Warp w owns the
+        //      rows w + NW i (i < 8); all eight rows' loads are issued first.
+        float sq[TM / NW];
+#pragma unroll
+        for (int i = 0; i < TM / NW; ++i) sq[i] = 0.f;
+        for (int cb = 0; cb < nchunk; cb += 32) {
+            const int c = cb + lane;
+            float4 v0[TM / NW], v1[TM / NW];
+#pragma unroll
+            for (int i = 0; i < TM / NW; ++i) {
+                const int64_t n = n0 + warp + NW * i;
+                v0[i] = v1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (c < nchunk && n < N) {
                     const float4 *row = reinterpret_cast<const float4 *>(Y + n * D + 8 * c);
-                    v0 = __ldg(row);
-                    v1 = __ldg(row + 1);
+                    v0[i] = __ldg(row);
+                    v1[i] = __ldg(row + 1);
                 }
-                sq = fmaf(v0.x, v0.x, sq); sq = fmaf(v0.y, v0.y, sq);
-                sq = fmaf(v0.z, v0.z, sq); sq = fmaf(v0.w, v0.w, sq);
-                sq = fmaf(v1.x, v1.x, sq); sq = fmaf(v1.y, v1.y, sq);
-                sq = fmaf(v1.z, v1.z, sq); sq = fmaf(v1.w, v1.w, sq);
-                __nv_bfloat162 b0 = __floats2bfloat162_rn(v0.x, v0.y);
-                __nv_bfloat162 b1 = __floats2bfloat162_rn(v0.z, v0.w);
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(v1.x, v1.y);
-                __nv_bfloat162 b3 = __floats2bfloat162_rn(v1.z, v1.w);
-                uint4 pk;
-                pk.x = *reinterpret_cast<uint32_t *>(&b0);
-                pk.y = *reinterpret_cast<uint32_t *>(&b1);
-                pk.z = *reinterpret_cast<uint32_t *>(&b2);
-                pk.w = *reinterpret_cast<uint32_t *>(&b3);
-                *reinterpret_cast<uint4 *>(Ysm + opnd_off(r, c, TM)) = pk;
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            for (int i = 0; i < TM / NW; ++i) {
+                float q = sq[i];
+                q = fmaf(v0[i].x, v0[i].x, q); q = fmaf(v0[i].y, v0[i].y, q);
+                q = fmaf(v0[i].z, v0[i].z, q); q = fmaf(v0[i].w, v0[i].w, q);
+                q = fmaf(v1[i].x, v1[i].x, q); q = fmaf(v1[i].y, v1[i].y, q);
+                q = fmaf(v1[i].z, v1[i].z, q); q = fmaf(v1[i].w, v1[i].w, q);
+                sq[i] = q;
+                if (c < nchunk) {
+                    __nv_bfloat162 b0 = __floats2bfloat162_rn(v0[i].x, v0[i].y);
+                    __nv_bfloat162 b1 = __floats2bfloat162_rn(v0[i].z, v0[i].w);
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v1[i].x, v1[i].y);
+                    __nv_bfloat162 b3 = __floats2bfloat162_rn(v1[i].z, v1[i].w);
+                    uint4 pk;
+                    pk.x = *reinterpret_cast<uint32_t *>(&b0);
+                    pk.y = *reinterpret_cast<uint32_t *>(&b1);
+                    pk.z = *reinterpret_cast<uint32_t *>(&b2);
+                    pk.w = *reinterpret_cast<uint32_t *>(&b3);
+                    *reinterpret_cast<uint4 *>(Ysm + opnd_off(warp + NW * i, c, TM)) = pk;
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TM / NW; ++i) {
+            float q = sq[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+            const int64_t n = n0 + warp + NW * i;
             if (lane == 0 && n < N) {
-                yy_out[n] = make_float2(sq, 0.f);
-                if (!isfinite(sq)) atomicOr(status, ST_NONFINITE);
+                yy_out[n] = make_float2(q, 0.f);
+                if (!isfinite(q)) atomicOr(status, ST_NONFINITE);
             }
         }
         fence_proxy_async();
@@ -192,14 +224,29 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 const int p = warp * (64 / NW) + i;
                 const int64_t n = n0 + 64 * half + p;
                 if (n >= N) break;
-                unsigned key[8];
+                // packed keys: score key rounded down to 24 bits, then 255 - h, so
+                // that one 32-bit maximum ranks by score and breaks ties to the
+                // lower h (H <= 256); 0 marks an absent latent
+                const float *prow_p = Psm + pidx(p, lane, H);   // + 32 j for h = lane + 32 j
+                unsigned pk[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int h = lane + 32 * j;
-                    key[j] = h < H ? score_key(Psm[pidx(p, h, H)] * rn[j]) : 0u;
+                    pk[j] = h < H ? (score_key(prow_p[32 * j] * rn[j]) & 0xFFFFFF00u) | (unsigned)(255 - h)
+                                  : 0u;
                 }
-                // top-Hp, exact ties to the lower h (same rule as the FP32 path)
-                const int myh = warp_topk(key, Hp, lane, topk_scratch[warp]);
+                sort8_desc(pk);
+                // Hp rounds of the warp maximum; the winning lane pops its head
+                int myh = 0;
+                for (int r = 0; r < Hp; ++r) {
+                    const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
+                    if (lane == r) myh = 255 - (int)(w & 0xFFu);
+                    if (pk[0] == w) {
+#pragma unroll
+                        for (int j = 0; j < 7; ++j) pk[j] = pk[j + 1];
+                        pk[7] = 0u;
+                    }
+                }
                 // FP32 rescore: partial dot products over this lane's d, then a
                 // transposed warp reduction (16 slots -> one total per lane pair)
                 float v[16];
