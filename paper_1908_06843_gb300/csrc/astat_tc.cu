@@ -50,8 +50,9 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
     const int Hpad = halves * 128;
     unsigned char *Ehi = sb;                           // Hpad rows x 128 B
     unsigned char *Elo = Ehi + Hpad * 128;
-    unsigned char *Yhi = Elo + Hpad * 128;             // D rows x 128 B
-    unsigned char *Ylo = Yhi + D * 128;
+    // two Y buffers (hi, lo each D rows x 128 B): the next tile's Y is built
+    // while the tensor cores read the current one
+    unsigned char *Ybuf = Elo + Hpad * 128;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ntiles = (N + AT_T - 1) / AT_T;
     const uint32_t idesc = idesc_bf16(128, D);
@@ -71,26 +72,35 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    // E starts zeroed once; afterwards every point column is cleared by the
-    // thread that owns it (thread t < 64 writes only column t)
+    // E starts zeroed once; afterwards every entry is cleared by the thread
+    // that wrote it
     {
         uint4 *z = reinterpret_cast<uint4 *>(Ehi);
         const int nz = 2 * Hpad * 128 / 16;
         for (int i = tid; i < nz; i += AT_NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
     }
-    int prev_h[PROSPER_MAX_HPRIME];
+    int prev_h[(PROSPER_MAX_HPRIME + 3) / 4];
 #pragma unroll
-    for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) prev_h[j] = -1;
+    for (int j = 0; j < (PROSPER_MAX_HPRIME + 3) / 4; ++j) prev_h[j] = -1;
 
     // Y of a tile in registers: work item w = (4 consecutive d, 8-point chunk c)
+    // with c = 4 ((w >> 2) / (D/4)) + (w & 3), d = 4 ((w >> 2) % (D/4)) + 0..3: a
+    // warp's loads cover 4 point rows x 128 contiguous bytes, and the 8 lanes of
+    // one shared-memory store wavefront write 8 different swizzle chunk positions
     const int items = (D / 4) * (AT_T / 8);            // <= 512 for D <= 256
     float4 yv[2][8];
+    auto item_cd = [&](int w, int &c, int &d4) {
+        const int rest = w >> 2;
+        d4 = (rest % (D / 4)) * 4;
+        c = 4 * (rest / (D / 4)) + (w & 3);
+    };
     auto prefetch = [&](int64_t t) {
         const int64_t base = t * AT_T;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int w = tid + AT_NT * r;
-            const int d4 = (w % (D / 4)) * 4, c = w / (D / 4);
+            int c, d4;
+            item_cd(w, c, d4);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int64_t n = base + 8 * c + i;
@@ -100,57 +110,32 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
         }
     };
 
-    // the tile's candidate lists and posterior means (thread t < 64: point t)
-    int sh[PROSPER_MAX_HPRIME];
-    float sv[PROSPER_MAX_HPRIME];
+    // the tile's candidate lists and posterior means: thread t handles point
+    // t % 64 and its entries j = t / 64 + 4 i
+    constexpr int EPT = (PROSPER_MAX_HPRIME + 3) / 4;   // entries per thread
+    const int ept_j0 = tid / AT_T, ept_p = tid % AT_T;
+    int sh[EPT];
+    float sv[EPT];
     auto prefetch_e = [&](int64_t t) {
-        const int64_t n = t * AT_T + tid;
+        const int64_t n = t * AT_T + ept_p;
 #pragma unroll
-        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
-            const bool ok = tid < AT_T && n < N && j < Hp;
-            sh[j] = ok ? min(max(__ldg(sel + n * SEL_STRIDE + j), 0), H - 1) : -1;
-            sv[j] = ok ? __ldg(es + n * SEL_STRIDE + j) : 0.f;
+        for (int i = 0; i < EPT; ++i) {
+            const int j = ept_j0 + 4 * i;
+            const bool ok = n < N && j < Hp;
+            sh[i] = ok ? min(max(__ldg(sel + n * SEL_STRIDE + j), 0), H - 1) : -1;
+            sv[i] = ok ? __ldg(es + n * SEL_STRIDE + j) : 0.f;
         }
     };
 
-    uint32_t phase = 0;
-    bool aborted = false;
-    int done_tiles = 0;
-    int64_t tile = blockIdx.x;
-    if (tile < ntiles) {
-        prefetch(tile);
-        prefetch_e(tile);
-    }
-    __syncthreads();
-    for (; tile < ntiles; tile += gridDim.x) {
-        // ---- E operand: clear this column's previous entries, write the new ones
-        if (tid < AT_T) {
-#pragma unroll
-            for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
-                if (prev_h[j] >= 0) {
-                    const uint32_t off = kmaj_off(prev_h[j], tid);
-                    *reinterpret_cast<uint16_t *>(Ehi + off) = 0;
-                    *reinterpret_cast<uint16_t *>(Elo + off) = 0;
-                    prev_h[j] = -1;
-                }
-#pragma unroll
-            for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
-                const int h = sh[j];
-                if (h < 0) continue;
-                __nv_bfloat16 hi, lo;
-                split_bf16(sv[j], hi, lo);
-                const uint32_t off = kmaj_off(h, tid);
-                *reinterpret_cast<__nv_bfloat16 *>(Ehi + off) = hi;
-                *reinterpret_cast<__nv_bfloat16 *>(Elo + off) = lo;
-                prev_h[j] = h;
-            }
-        }
-        // ---- Y operand, transposed (points contiguous), hi and lo parts
+    // Y of the prefetched tile (registers) -> hi and lo operands, transposed
+    // (points contiguous)
+    auto build_y = [&](unsigned char *Yhi, unsigned char *Ylo) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int w = tid + AT_NT * r;
             if (w >= items) continue;
-            const int d4 = (w % (D / 4)) * 4, c = w / (D / 4);
+            int c, d4;
+            item_cd(w, c, d4);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 uint32_t ph[4], pl[4];
@@ -170,6 +155,44 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
                 *reinterpret_cast<uint4 *>(Ylo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
             }
         }
+    };
+
+    uint32_t phase = 0;
+    bool aborted = false;
+    int done_tiles = 0;
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) {
+        prefetch(tile);
+        prefetch_e(tile);
+        build_y(Ybuf, Ybuf + D * 128);
+        if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+    }
+    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+        unsigned char *Yhi = Ybuf + (size_t)(it & 1) * 2 * D * 128, *Ylo = Yhi + D * 128;
+        // ---- E operand: clear this column's previous entries, write the new ones
+        //      (the previous tile's MMA chain has completed)
+        // (the entries of one point are distinct latents, so the four threads of
+        // a point never write the same element)
+#pragma unroll
+        for (int i = 0; i < EPT; ++i)
+            if (prev_h[i] >= 0) {
+                const uint32_t off = kmaj_off(prev_h[i], ept_p);
+                *reinterpret_cast<uint16_t *>(Ehi + off) = 0;
+                *reinterpret_cast<uint16_t *>(Elo + off) = 0;
+                prev_h[i] = -1;
+            }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+            const int h = sh[i];
+            if (h < 0) continue;
+            __nv_bfloat16 hi, lo;
+            split_bf16(sv[i], hi, lo);
+            const uint32_t off = kmaj_off(h, ept_p);
+            *reinterpret_cast<__nv_bfloat16 *>(Ehi + off) = hi;
+            *reinterpret_cast<__nv_bfloat16 *>(Elo + off) = lo;
+            prev_h[i] = h;
+        }
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -188,10 +211,14 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
             }
             umma_commit(bar);
         }
-        // the next tile's data travel while the tensor cores work
+        // while the tensor cores work: the next tile's Y operand goes into the
+        // other buffer (last read by the previous, completed chain), and the
+        // data of the tile after it start to travel
         if (tile + gridDim.x < ntiles) {
-            prefetch(tile + gridDim.x);
+            unsigned char *Yn = Ybuf + (size_t)((it + 1) & 1) * 2 * D * 128;
+            build_y(Yn, Yn + D * 128);
             prefetch_e(tile + gridDim.x);
+            if (tile + 2 * (int64_t)gridDim.x < ntiles) prefetch(tile + 2 * (int64_t)gridDim.x);
         }
         const bool ok = mbar_wait(bar, phase, kAtWaitNs);
         phase ^= 1u;
@@ -258,7 +285,7 @@ int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaS
     if (N <= 0) return PROSPER_OK;
     const int D = c->D, H = c->H;
     const int halves = (H + 127) / 128;
-    const size_t smem = 1024 + (size_t)2 * halves * 128 * 128 + (size_t)2 * D * 128;
+    const size_t smem = 1024 + (size_t)2 * halves * 128 * 128 + (size_t)4 * D * 128;
     static size_t attr = 0;
     if (smem > attr) {
         PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_astat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
