@@ -25,7 +25,8 @@ namespace {
 using namespace tc;
 
 constexpr int AT_T = 64;      // points per tile (one 128-byte K atom of BF16)
-constexpr int AT_NT = 256;    // threads per CTA
+constexpr int AT_CW = 8;      // converter warps (+ one control warp)
+constexpr int AT_NT = 32 * (AT_CW + 1);
 constexpr unsigned long long kAtWaitNs = 2000000000ull;
 
 // byte offset of element (row r, point k) in a K-major 64-wide swizzled operand
@@ -43,23 +44,27 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
            int64_t N, int D, int H, int Hp, int halves, uint32_t tmem_cols, float *__restrict__ part,
            unsigned *__restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t lbar[2], cbar[2];   // data of half q arrived / MMAs of half q done
     __shared__ uint32_t tmem_slot;
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *sb = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const int Hpad = halves * 128;
-    unsigned char *Ehi = sb;                           // Hpad rows x 128 B
+    const int SP = D * 4 + 16;                          // staging row pitch (bytes)
+    unsigned char *Ehi = sb;                            // Hpad rows x 128 B
     unsigned char *Elo = Ehi + Hpad * 128;
-    // two Y buffers (hi, lo each D rows x 128 B): the next tile's Y is built
-    // while the tensor cores read the current one
-    unsigned char *Ybuf = Elo + Hpad * 128;
+    unsigned char *Yhi = Elo + Hpad * 128;              // D rows x 128 B
+    unsigned char *Ylo = Yhi + D * 128;
+    unsigned char *Stg = Ylo + D * 128;                 // AT_T rows x SP bytes (FP32 Y)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool conv = warp < AT_CW;                     // converter warps; warp AT_CW controls
     const int64_t ntiles = (N + AT_T - 1) / AT_T;
     const uint32_t idesc = idesc_bf16(128, D);
-    const uint32_t bar = smem_u32(&mbar);
 
     if (tid == 0) {
-        mbar_init(bar, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(smem_u32(&lbar[q]), 1);
+            mbar_init(smem_u32(&cbar[q]), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -67,11 +72,6 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
                      ::"r"(smem_u32(&tmem_slot)), "r"(tmem_cols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-
     // E starts zeroed once; afterwards every entry is cleared by the thread
     // that wrote it
     {
@@ -79,162 +79,186 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
         const int nz = 2 * Hpad * 128 / 16;
         for (int i = tid; i < nz; i += AT_NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
     }
-    int prev_h[(PROSPER_MAX_HPRIME + 3) / 4];
-#pragma unroll
-    for (int j = 0; j < (PROSPER_MAX_HPRIME + 3) / 4; ++j) prev_h[j] = -1;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
 
-    // Y of a tile in registers: work item w = (4 consecutive d, 8-point chunk c)
-    // with c = 4 ((w >> 2) / (D/4)) + (w & 3), d = 4 ((w >> 2) % (D/4)) + 0..3: a
-    // warp's loads cover 4 point rows x 128 contiguous bytes, and the 8 lanes of
-    // one shared-memory store wavefront write 8 different swizzle chunk positions
-    const int items = (D / 4) * (AT_T / 8);            // <= 512 for D <= 256
-    float4 yv[2][8];
-    auto item_cd = [&](int w, int &c, int &d4) {
-        const int rest = w >> 2;
-        d4 = (rest % (D / 4)) * 4;
-        c = 4 * (rest / (D / 4)) + (w & 3);
-    };
-    auto prefetch = [&](int64_t t) {
-        const int64_t base = t * AT_T;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int w = tid + AT_NT * r;
-            int c, d4;
-            item_cd(w, c, d4);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t n = base + 8 * c + i;
-                yv[r][i] = (w < items && n < N) ? __ldg(reinterpret_cast<const float4 *>(Y + n * D + d4))
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
+    // control warp: rows [32 q, 32 q + 32) of tile t into the staging rows, one
+    // bulk copy of D floats per row (lane r copies row 32 q + r)
+    auto load_half = [&](int64_t t, int q) {
+        const int64_t n = t * AT_T + 32 * q + lane;
+        const int64_t left = N - (t * AT_T + 32 * q);
+        const int rows = (int)(left < 0 ? 0 : (left > 32 ? 32 : left));
+        const uint32_t lb = smem_u32(&lbar[q]);
+        if (lane == 0) mbar_arrive_expect_tx(lb, (uint32_t)(rows * D * 4));
+        __syncwarp();
+        if (lane < rows)
+            bulk_g2s(smem_u32(Stg + (size_t)(32 * q + lane) * SP), Y + n * D, (uint32_t)(D * 4), lb);
     };
 
-    // the tile's candidate lists and posterior means: thread t handles point
-    // t % 64 and its entries j = t / 64 + 4 i
-    constexpr int EPT = (PROSPER_MAX_HPRIME + 3) / 4;   // entries per thread
-    const int ept_j0 = tid / AT_T, ept_p = tid % AT_T;
+    // converter item (one per thread and half): 4 consecutive d x 8 points.
+    // Within each 8-lane store wavefront the 8 lanes take 8 consecutive d4 and
+    // chunks c rotated so that both the staging reads (row pitch D*4+16) and
+    // the swizzled operand writes touch 8 different 16-byte bank groups.
+    const int G = D / 32;
+    int it_d4 = 0, it_c = 0;
+    {
+        const int wf = tid >> 3, l8 = tid & 7;
+        const int g = wf % G, rot = wf / G;             // rot in 0..3 for tid < D
+        it_d4 = 4 * (8 * g + l8);
+        it_c = ((l8 >> 1) + rot) & 3;                   // + 4 q
+    }
+    const bool has_item = conv && tid < D;
+
+    // E entries: point 32 q + (tid & 31), candidate slots j = tid/32 and tid/32 + 8
+    constexpr int EPT = (PROSPER_MAX_HPRIME + 7) / 8;
+    int prev_h[2][EPT];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) prev_h[q][i] = -1;
     int sh[EPT];
     float sv[EPT];
-    auto prefetch_e = [&](int64_t t) {
-        const int64_t n = t * AT_T + ept_p;
+    auto fetch_e = [&](int64_t t, int q) {
+        const int64_t n = t * AT_T + 32 * q + lane;
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
-            const int j = ept_j0 + 4 * i;
-            const bool ok = n < N && j < Hp;
+            const int j = warp + 8 * i;
+            const bool ok = conv && t < ntiles && n < N && j < Hp;
             sh[i] = ok ? min(max(__ldg(sel + n * SEL_STRIDE + j), 0), H - 1) : -1;
             sv[i] = ok ? __ldg(es + n * SEL_STRIDE + j) : 0.f;
         }
     };
 
-    // Y of the prefetched tile (registers) -> hi and lo operands, transposed
-    // (points contiguous)
-    auto build_y = [&](unsigned char *Yhi, unsigned char *Ylo) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int w = tid + AT_NT * r;
-            if (w >= items) continue;
-            int c, d4;
-            item_cd(w, c, d4);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                uint32_t ph[4], pl[4];
-#pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    const float a = e == 0 ? yv[r][i].x : e == 1 ? yv[r][i].y : e == 2 ? yv[r][i].z : yv[r][i].w;
-                    const float b = e == 0 ? yv[r][i + 1].x : e == 1 ? yv[r][i + 1].y : e == 2 ? yv[r][i + 1].z : yv[r][i + 1].w;
-                    __nv_bfloat16 ah, al, bh, bl;
-                    split_bf16(a, ah, al);
-                    split_bf16(b, bh, bl);
-                    ph[i >> 1] = (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
-                    pl[i >> 1] = (uint32_t)__bfloat16_as_ushort(al) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
-                }
-                const int d = d4 + e;
-                const uint32_t off = (uint32_t)(d * 128 + ((c ^ (d & 7)) << 4));
-                *reinterpret_cast<uint4 *>(Yhi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                *reinterpret_cast<uint4 *>(Ylo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-            }
-        }
-    };
-
-    uint32_t phase = 0;
     bool aborted = false;
     int done_tiles = 0;
     int64_t tile = blockIdx.x;
-    if (tile < ntiles) {
-        prefetch(tile);
-        prefetch_e(tile);
-        build_y(Ybuf, Ybuf + D * 128);
-        if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
+    if (warp == AT_CW && tile < ntiles) {
+        load_half(tile, 0);
+        load_half(tile, 1);
     }
-    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
-        unsigned char *Yhi = Ybuf + (size_t)(it & 1) * 2 * D * 128, *Ylo = Yhi + D * 128;
-        // ---- E operand: clear this column's previous entries, write the new ones
-        //      (the previous tile's MMA chain has completed)
-        // (the entries of one point are distinct latents, so the four threads of
-        // a point never write the same element)
+    fetch_e(tile, 0);
+    for (int it = 0; tile < ntiles && !aborted; ++it, tile += gridDim.x) {
 #pragma unroll
-        for (int i = 0; i < EPT; ++i)
-            if (prev_h[i] >= 0) {
-                const uint32_t off = kmaj_off(prev_h[i], ept_p);
-                *reinterpret_cast<uint16_t *>(Ehi + off) = 0;
-                *reinterpret_cast<uint16_t *>(Elo + off) = 0;
-                prev_h[i] = -1;
-            }
-        __syncthreads();
+        for (int q = 0; q < 2; ++q) {
+            bool ok = true;
+            if (conv) {
+                ok = mbar_wait(smem_u32(&lbar[q]), (uint32_t)(it & 1), kAtWaitNs);
+                if (ok && it > 0) ok = mbar_wait(smem_u32(&cbar[q]), (uint32_t)((it - 1) & 1), kAtWaitNs);
+                tc_fence_after();
+                // E columns of this half: clear the previous tile's entries, then
+                // write the new ones.  The converter warps meet in between (a
+                // latent may move between candidate slots of a point), and the
+                // meeting also makes the wait outcome uniform among them.
+                const int p = 32 * q + lane;
+                if (ok) {
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-            const int h = sh[i];
-            if (h < 0) continue;
-            __nv_bfloat16 hi, lo;
-            split_bf16(sv[i], hi, lo);
-            const uint32_t off = kmaj_off(h, ept_p);
-            *reinterpret_cast<__nv_bfloat16 *>(Ehi + off) = hi;
-            *reinterpret_cast<__nv_bfloat16 *>(Elo + off) = lo;
-            prev_h[i] = h;
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t eh = smem_u32(Ehi), el = smem_u32(Elo), yh = smem_u32(Yhi), yl = smem_u32(Ylo);
-            for (int hf = 0; hf < halves; ++hf) {
-                const uint32_t d_tm = tmem + (uint32_t)(hf * D);
-#pragma unroll
-                for (int ks = 0; ks < AT_T / 16; ++ks) {
-                    const uint32_t ao = (uint32_t)(hf * 128 * 128 + ks * 32), bo = (uint32_t)(ks * 32);
-                    umma_bf16(d_tm, desc_sw128(eh + ao), desc_sw128(yh + bo), idesc,
-                              (done_tiles > 0 || ks > 0) ? 1u : 0u);
-                    umma_bf16(d_tm, desc_sw128(eh + ao), desc_sw128(yl + bo), idesc, 1u);
-                    umma_bf16(d_tm, desc_sw128(el + ao), desc_sw128(yh + bo), idesc, 1u);
+                    for (int i = 0; i < EPT; ++i)
+                        if (prev_h[q][i] >= 0) {
+                            const uint32_t off = kmaj_off(prev_h[q][i], p);
+                            *reinterpret_cast<uint16_t *>(Ehi + off) = 0;
+                            *reinterpret_cast<uint16_t *>(Elo + off) = 0;
+                            prev_h[q][i] = -1;
+                        }
                 }
+                {
+                    unsigned anyfail;
+                    asm volatile("{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n"
+                                 " bar.red.or.pred po, 1, %2, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+                                 : "=r"(anyfail) : "r"((unsigned)!ok), "r"(AT_CW * 32) : "memory");
+                    ok = !anyfail;
+                }
+                if (ok) {
+#pragma unroll
+                    for (int i = 0; i < EPT; ++i) {
+                        const int h = sh[i];
+                        if (h < 0) continue;
+                        __nv_bfloat16 hi, lo;
+                        split_bf16(sv[i], hi, lo);
+                        const uint32_t off = kmaj_off(h, p);
+                        *reinterpret_cast<__nv_bfloat16 *>(Ehi + off) = hi;
+                        *reinterpret_cast<__nv_bfloat16 *>(Elo + off) = lo;
+                        prev_h[q][i] = h;
+                    }
+                    // Y of this half: FP32 staging -> BF16 hi / lo, transposed
+                    if (has_item) {
+                        const int c = 4 * q + it_c;
+                        const int64_t n0 = tile * AT_T + 8 * c;
+                        float4 v[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            v[i] = (n0 + i < N) ? *reinterpret_cast<const float4 *>(Stg + (size_t)(8 * c + i) * SP + it_d4 * 4)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            uint32_t ph[4], pl[4];
+#pragma unroll
+                            for (int i = 0; i < 8; i += 2) {
+                                const float x0 = e == 0 ? v[i].x : e == 1 ? v[i].y : e == 2 ? v[i].z : v[i].w;
+                                const float x1 = e == 0 ? v[i + 1].x : e == 1 ? v[i + 1].y : e == 2 ? v[i + 1].z : v[i + 1].w;
+                                __nv_bfloat16 ah, al, bh, bl;
+                                split_bf16(x0, ah, al);
+                                split_bf16(x1, bh, bl);
+                                ph[i >> 1] = (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
+                                pl[i >> 1] = (uint32_t)__bfloat16_as_ushort(al) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
+                            }
+                            const int d = it_d4 + e;
+                            const uint32_t off = (uint32_t)(d * 128 + ((c ^ (d & 7)) << 4));
+                            *reinterpret_cast<uint4 *>(Yhi + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                            *reinterpret_cast<uint4 *>(Ylo + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                        }
+                    }
+                }
+                // candidate lists of the next half travel while the rest proceeds
+                if (q == 0) fetch_e(tile, 1);
+                else fetch_e(tile + gridDim.x, 0);
             }
-            umma_commit(bar);
+            fence_proxy_async();
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+                aborted = true;
+                break;
+            }
+            if (warp == AT_CW) {
+                // the staging rows of this half are free again: next tile's rows
+                if (tile + gridDim.x < ntiles) load_half(tile + gridDim.x, q);
+                if (lane == 0) {
+                    tc_fence_after();
+                    const uint32_t eh = smem_u32(Ehi), el = smem_u32(Elo), yh = smem_u32(Yhi), yl = smem_u32(Ylo);
+                    for (int hf = 0; hf < halves; ++hf) {
+                        const uint32_t d_tm = tmem + (uint32_t)(hf * D);
+#pragma unroll
+                        for (int k2 = 0; k2 < 2; ++k2) {
+                            const int ks = 2 * q + k2;
+                            const uint32_t ao = (uint32_t)(hf * 128 * 128 + ks * 32), bo = (uint32_t)(ks * 32);
+                            umma_bf16(d_tm, desc_sw128(eh + ao), desc_sw128(yh + bo), idesc,
+                                      (it > 0 || ks > 0) ? 1u : 0u);
+                            umma_bf16(d_tm, desc_sw128(eh + ao), desc_sw128(yl + bo), idesc, 1u);
+                            umma_bf16(d_tm, desc_sw128(el + ao), desc_sw128(yh + bo), idesc, 1u);
+                        }
+                    }
+                    umma_commit(smem_u32(&cbar[q]));
+                }
+                __syncwarp();
+            }
         }
-        // while the tensor cores work: the next tile's Y operand goes into the
-        // other buffer (last read by the previous, completed chain), and the
-        // data of the tile after it start to travel
-        if (tile + gridDim.x < ntiles) {
-            unsigned char *Yn = Ybuf + (size_t)((it + 1) & 1) * 2 * D * 128;
-            build_y(Yn, Yn + D * 128);
-            prefetch_e(tile + gridDim.x);
-            if (tile + 2 * (int64_t)gridDim.x < ntiles) prefetch(tile + 2 * (int64_t)gridDim.x);
-        }
-        const bool ok = mbar_wait(bar, phase, kAtWaitNs);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
-            aborted = true;
-            break;
-        }
-        tc_fence_after();
-        ++done_tiles;
+        if (!aborted) ++done_tiles;
+    }
+    // the last chain (half 1 of the last tile) covers every MMA of this CTA
+    bool ok_end = true;
+    if (done_tiles > 0)
+        ok_end = mbar_wait(smem_u32(&cbar[1]), (uint32_t)((done_tiles - 1) & 1), kAtWaitNs);
+    tc_fence_after();
+    if (__syncthreads_or(!ok_end)) {
+        if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+        aborted = true;
     }
     // ---- epilogue: this CTA's FP32 partial of A^T to global memory (plain
     //      stores; k_reduce_parts sums the partials in FP64 in a fixed order)
-    if (!aborted) {
-        const int q = warp & 3;
-        const int h_in = q * 32 + lane;
+    if (!aborted && conv) {
+        const int qd = warp & 3;
+        const int h_in = qd * 32 + lane;
         const int cb = (warp < 4) ? 0 : D / 2, ce = (warp < 4) ? D / 2 : D;
         float *mine = part + (size_t)blockIdx.x * H * D;
         for (int hf = 0; hf < halves; ++hf) {
@@ -242,7 +266,7 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
             for (int c0 = cb; c0 < ce; c0 += 16) {
                 float v[16];
                 if (done_tiles > 0) {
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hf * D + c0), v);
+                    tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(hf * D + c0), v);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) v[k] = 0.f;
@@ -255,7 +279,16 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
             }
         }
     }
-    if (aborted && tid == 0) mbar_wait(bar, phase ^ 1u, kAtWaitNs / 2);
+    if (aborted && tid == 0) {
+        // let copies and MMA chains still in flight finish (bounded) before
+        // the shared and tensor memory are released
+        for (int q = 0; q < 2; ++q) {
+            mbar_wait(smem_u32(&lbar[q]), 0u, kAtWaitNs / 8);
+            mbar_wait(smem_u32(&lbar[q]), 1u, kAtWaitNs / 8);
+            mbar_wait(smem_u32(&cbar[q]), 0u, kAtWaitNs / 8);
+            mbar_wait(smem_u32(&cbar[q]), 1u, kAtWaitNs / 8);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -285,7 +318,8 @@ int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaS
     if (N <= 0) return PROSPER_OK;
     const int D = c->D, H = c->H;
     const int halves = (H + 127) / 128;
-    const size_t smem = 1024 + (size_t)2 * halves * 128 * 128 + (size_t)4 * D * 128;
+    const size_t smem = 1024 + (size_t)2 * halves * 128 * 128 + (size_t)2 * D * 128 +
+                        (size_t)AT_T * (D * 4 + 16);
     static size_t attr = 0;
     if (smem > attr) {
         PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_astat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -32,6 +32,17 @@ static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, 
         if (gtime_ns() - t0 > limit_ns) return false;
     }
 }
+// One arrival that also announces `bytes` of asynchronous transfers to come.
+static __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                 ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16);
+// completion is counted on the mbarrier in bytes.
+static __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
 static __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
