@@ -34,6 +34,16 @@ __device__ __forceinline__ uint32_t kmaj_off(int r, int k) {
     return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7))) << 4) + ((k & 7) << 1));
 }
 
+// the same split for two values at once: packed BF16 pairs (x0 in the low half)
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t &hi2, uint32_t &lo2) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    hi2 = *reinterpret_cast<const uint32_t *>(&h);
+    const float r0 = x0 - __uint_as_float(hi2 << 16);
+    const float r1 = x1 - __uint_as_float(hi2 & 0xFFFF0000u);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(r0, r1);
+    lo2 = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
     hi = __float2bfloat16_rn(x);
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
@@ -49,7 +59,7 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *sb = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const int Hpad = halves * 128;
-    const int SP = D * 4 + 16;                          // staging row pitch (bytes)
+    const int SP = D * 4;                               // staging row pitch (bytes)
     unsigned char *Ehi = sb;                            // Hpad rows x 128 B
     unsigned char *Elo = Ehi + Hpad * 128;
     unsigned char *Yhi = Elo + Hpad * 128;              // D rows x 128 B
@@ -84,23 +94,25 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    // control warp: rows [32 q, 32 q + 32) of tile t into the staging rows, one
-    // bulk copy of D floats per row (lane r copies row 32 q + r)
+    // control warp: rows [32 q, 32 q + 32) of tile t into the staging rows
+    // (contiguous in Y and in shared memory: one bulk copy)
     auto load_half = [&](int64_t t, int q) {
-        const int64_t n = t * AT_T + 32 * q + lane;
-        const int64_t left = N - (t * AT_T + 32 * q);
-        const int rows = (int)(left < 0 ? 0 : (left > 32 ? 32 : left));
-        const uint32_t lb = smem_u32(&lbar[q]);
-        if (lane == 0) mbar_arrive_expect_tx(lb, (uint32_t)(rows * D * 4));
+        if (lane == 0) {
+            const int64_t r0 = t * AT_T + 32 * q;
+            const int64_t left = N - r0;
+            const int rows = (int)(left < 0 ? 0 : (left > 32 ? 32 : left));
+            const uint32_t lb = smem_u32(&lbar[q]);
+            mbar_arrive_expect_tx(lb, (uint32_t)(rows * D * 4));
+            if (rows > 0) bulk_g2s(smem_u32(Stg + (size_t)(32 * q) * SP), Y + r0 * D, (uint32_t)(rows * D * 4), lb);
+        }
         __syncwarp();
-        if (lane < rows)
-            bulk_g2s(smem_u32(Stg + (size_t)(32 * q + lane) * SP), Y + n * D, (uint32_t)(D * 4), lb);
     };
 
     // converter item (one per thread and half): 4 consecutive d x 8 points.
     // Within each 8-lane store wavefront the 8 lanes take 8 consecutive d4 and
-    // chunks c rotated so that both the staging reads (row pitch D*4+16) and
-    // the swizzled operand writes touch 8 different 16-byte bank groups.
+    // chunks c rotated so that both the staging reads (dense rows of D floats,
+    // D a multiple of 32) and the swizzled operand writes touch 8 different
+    // 16-byte bank groups.
     const int G = D / 32;
     int it_d4 = 0, it_c = 0;
     {
@@ -197,11 +209,7 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
                             for (int i = 0; i < 8; i += 2) {
                                 const float x0 = e == 0 ? v[i].x : e == 1 ? v[i].y : e == 2 ? v[i].z : v[i].w;
                                 const float x1 = e == 0 ? v[i + 1].x : e == 1 ? v[i + 1].y : e == 2 ? v[i + 1].z : v[i + 1].w;
-                                __nv_bfloat16 ah, al, bh, bl;
-                                split_bf16(x0, ah, al);
-                                split_bf16(x1, bh, bl);
-                                ph[i >> 1] = (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
-                                pl[i >> 1] = (uint32_t)__bfloat16_as_ushort(al) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
+                                split_bf16x2(x0, x1, ph[i >> 1], pl[i >> 1]);
                             }
                             const int d = it_d4 + e;
                             const uint32_t off = (uint32_t)(d * 128 + ((c ^ (d & 7)) << 4));
@@ -319,7 +327,7 @@ int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaS
     const int D = c->D, H = c->H;
     const int halves = (H + 127) / 128;
     const size_t smem = 1024 + (size_t)2 * halves * 128 * 128 + (size_t)2 * D * 128 +
-                        (size_t)AT_T * (D * 4 + 16);
+                        (size_t)AT_T * D * 4;
     static size_t attr = 0;
     if (smem > attr) {
         PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_astat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
