@@ -53,6 +53,7 @@ KERNEL_WORK = {
     "bsc_proj_bf16": ("hbm", 4 * D, "byte"),              # Y read once (FP32)
     "bsc_states": ("alu", 3198 + 1276 + 2560 + 6745, "lane-op"),
     "astat": ("hbm", 4 * D + 8 * 16, "byte"),             # Y re-read + per-point records
+    "astat_tc": ("hbm", 4 * D + 8 * 16, "byte"),          # same work on the tensor cores
 }
 
 

@@ -284,6 +284,19 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
 // bit-reversed state mask (lower local unit = higher weight).
 #define crev_hi(t, LB, HP) ((int)(__brev((unsigned)(t) << (LB)) >> (32 - (HP))))
 
+// FP32 -> FP64 by the IEEE-754 field layout on the integer pipe (exact for
+// every normal float; subnormals become 0, infinities and NaNs keep their
+// class).  On this part the FP64 pipe issues one warp instruction per ~20
+// clocks per SM, so the 55 conversions per point of the B accumulation are
+// kept off it.
+__device__ __forceinline__ double f32_to_f64_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned m = (e == 0u) ? 0u : (u & 0x7FFFFFu);
+    const unsigned e64 = (e == 0u) ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
+    return __hiloint2double((int)((u & 0x80000000u) | (e64 << 20) | (m >> 3)), (int)(m << 29));
+}
+
 __device__ __forceinline__ float fast_ex2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -378,19 +391,50 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
     const bool valid = n < A.N;
     const int64_t nn = valid ? n : 0;
 
-    const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
-    const float lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634);
-    const float is2 = (float)(1.4426950408889634 / (sigma * sigma));
+    // per-call constants, formed once per CTA (FP64 logs and divisions are
+    // slow on this part):  lpi = log2e log(pi/(1-pi)),  is2 = log2e / sigma^2,
+    // log p(y, s=0) = c0 - y^T y / (2 sigma^2)
+    __shared__ float s_lpi, s_is2;
+    __shared__ double s_c0, s_inv2s2;
+    if (threadIdx.x == 0) {
+        const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
+        const double s2 = sigma * sigma;
+        s_lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634);
+        s_is2 = (float)(1.4426950408889634 / s2);
+        s_c0 = A.H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2));
+        s_inv2s2 = 0.5 / s2;
+    }
+    __syncthreads();
+    const float lpi = s_lpi, is2 = s_is2;
     const int gamma = A.gamma;
     const int H = A.H;
 
+    // candidate lists and their projections: rows of SEL_STRIDE (16) entries,
+    // 64-byte aligned, read as 16-byte vectors
+    constexpr int NV = (HP + 3) / 4;
     int I[HP];
+    float P[HP];
+    {
+        const int4 *sr = reinterpret_cast<const int4 *>(A.sel + nn * SEL_STRIDE);
+        const float4 *pr = reinterpret_cast<const float4 *>(A.selp + nn * SEL_STRIDE);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const int4 iv = sr[q];
+            const float4 pv = pr[q];
+            const int ia[4] = {iv.x, iv.y, iv.z, iv.w};
+            const float pa[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (4 * q + k < HP) {
+                    I[4 * q + k] = min(max(ia[k], 0), H - 1);   // defensive
+                    P[4 * q + k] = pa[k];
+                }
+        }
+    }
     float a[HP], b[HP][HP];
 #pragma unroll
-    for (int j = 0; j < HP; ++j) I[j] = min(max(A.sel[nn * SEL_STRIDE + j], 0), H - 1);   // defensive
-#pragma unroll
     for (int j = 0; j < HP; ++j) {
-        float pj = A.selp[nn * SEL_STRIDE + j];
+        float pj = P[j];
         float gjj = __ldg(A.G + (size_t)I[j] * H + I[j]);
         a[j] = lpi + (pj - 0.5f * gjj) * is2;
         b[j][j] = 0.f;
@@ -520,8 +564,7 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
 
     const float2 yyv = A.yy[nn];
     const double yy = (double)yyv.x + (double)yyv.y;
-    const double s2 = sigma * sigma;
-    const double logp0 = H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2)) - yy / (2.0 * s2);
+    const double logp0 = fma(-yy, s_inv2s2, s_c0);
     const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp0;
     // MAP state mask from the winning key
     const unsigned rmask = 0xFFFFu - (unsigned)(best & 0xFFFF);
@@ -552,37 +595,42 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
     }
 
     if (valid) {
+        float4 *er = reinterpret_cast<float4 *>(A.es + n * SEL_STRIDE);
 #pragma unroll
-        for (int j = 0; j < HP; ++j) A.es[n * SEL_STRIDE + j] = es[j];
+        for (int q = 0; q < NV; ++q)
+            er[q] = make_float4(es[4 * q], 4 * q + 1 < HP ? es[(4 * q + 1) % HP] : 0.f,
+                                4 * q + 2 < HP ? es[(4 * q + 2) % HP] : 0.f,
+                                4 * q + 3 < HP ? es[(4 * q + 3) % HP] : 0.f);
         // sum <s s^T> into the upper triangle of B (I ascending -> I_i < I_j)
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
             double *row = A.B + (size_t)I[i] * H;
 #pragma unroll
-            for (int j = i; j < HP; ++j) atomicAdd(row + I[j], (double)(S2[i][j] * invZ));
+            for (int j = i; j < HP; ++j) atomicAdd(row + I[j], f32_to_f64_bits(S2[i][j] * invZ));
         }
     }
-    // scalar statistics: warp reduction in FP64, one atomic per warp
-    double s1 = 0.0, f = 0.0, y2 = 0.0, cnt = 0.0;
+    // scalar statistics: warp sums (F and y^T y in FP64, sum <|s|> in FP32 over
+    // the 32 points, the count by ballot), one atomic per warp
+    float s1 = 0.f;
+    double f = 0.0, y2 = 0.0;
     if (valid) {
 #pragma unroll
         for (int j = 0; j < HP; ++j) s1 += es[j];
         f = logZ;
         y2 = yy;
-        cnt = 1.0;
     }
+    const unsigned cnt = __popc(__ballot_sync(0xffffffffu, valid));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         f += __shfl_xor_sync(0xffffffffu, f, o);
         y2 += __shfl_xor_sync(0xffffffffu, y2, o);
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
-    if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
+    if ((threadIdx.x & 31) == 0 && cnt > 0u) {
         atomicAdd(A.scal + PROSPER_SC_F, f);
-        atomicAdd(A.scal + PROSPER_SC_S1, s1);
+        atomicAdd(A.scal + PROSPER_SC_S1, (double)s1);
         atomicAdd(A.scal + PROSPER_SC_YY, y2);
-        atomicAdd(A.scal + PROSPER_SC_N, cnt);
+        atomicAdd(A.scal + PROSPER_SC_N, (double)cnt);
     }
 }
 
