@@ -381,7 +381,7 @@ struct StateArgs {
 // MAP state (the canonically first state with l == m, found by a min over the
 // key (|s| << 16) + 0xFFFF - bitreverse(s)).
 template <int HP, bool ENCODE>
-__global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
+__global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     constexpr int HB = HP < 5 ? HP : 5;
     constexpr int LB = HP - HB;
     constexpr int NT = 1 << HB;
@@ -503,28 +503,25 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
         PROSPER_P2_GROUP(3);
         PROSPER_P2_GROUP(4);
         PROSPER_P2_GROUP(5);
-        // R[u] = sum_{t contains u} e[t] and the total, by pairwise halving
+#pragma unroll
+        for (int t = 0; t < NT; ++t) Gacc[t] += e[t];
+        // R[u] = sum_{t contains u} e[t] and the total, by pairwise halving in place
         float R[HB];
         float Zlo;
         {
-            float cur[NT];
-#pragma unroll
-            for (int t = 0; t < NT; ++t) cur[t] = e[t];
 #pragma unroll
             for (int u = 0; u < HB; ++u) {
                 const int half = NT >> (u + 1);
                 float r = 0.f;
 #pragma unroll
                 for (int t = 0; t < half; ++t) {
-                    r += cur[2 * t + 1];
-                    cur[t] = cur[2 * t] + cur[2 * t + 1];
+                    r += e[2 * t + 1];
+                    e[t] = e[2 * t] + e[2 * t + 1];
                 }
                 R[u] = r;
             }
-            Zlo = cur[0];
+            Zlo = e[0];
         }
-#pragma unroll
-        for (int t = 0; t < NT; ++t) Gacc[t] += e[t];
 #pragma unroll
         for (int i = 0; i < LB; ++i) {
 #pragma unroll
@@ -601,12 +598,25 @@ __global__ void __launch_bounds__(256, 1) k_bsc_states(StateArgs A) {
             er[q] = make_float4(es[4 * q], 4 * q + 1 < HP ? es[(4 * q + 1) % HP] : 0.f,
                                 4 * q + 2 < HP ? es[(4 * q + 2) % HP] : 0.f,
                                 4 * q + 3 < HP ? es[(4 * q + 3) % HP] : 0.f);
-        // sum <s s^T> into the upper triangle of B (I ascending -> I_i < I_j)
+        // sum <s s^T> into the upper triangle of B (I ascending -> I_i < I_j);
+        // the candidate list is read again here rather than kept in registers
+        int J[HP];
+        {
+            const int4 *sr = reinterpret_cast<const int4 *>(A.sel + nn * SEL_STRIDE);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const int4 iv = sr[q];
+                const int ia[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (4 * q + k < HP) J[4 * q + k] = min(max(ia[k], 0), H - 1);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < HP; ++i) {
-            double *row = A.B + (size_t)I[i] * H;
+            double *row = A.B + (size_t)J[i] * H;
 #pragma unroll
-            for (int j = i; j < HP; ++j) atomicAdd(row + I[j], f32_to_f64_bits(S2[i][j] * invZ));
+            for (int j = i; j < HP; ++j) atomicAdd(row + J[j], f32_to_f64_bits(S2[i][j] * invZ));
         }
     }
     // scalar statistics: warp sums (F and y^T y in FP64, sum <|s|> in FP32 over
@@ -794,10 +804,10 @@ int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t 
 
 template <int HP>
 static int states_dispatch(StateArgs &A, bool encode, int64_t N, cudaStream_t s) {
-    int grid = (int)((N + 255) / 256);
+    int grid = (int)((N + 127) / 128);
     TraceScope tr(A.trace_ctx, encode ? "bsc_states_encode" : "bsc_states", s);
-    if (encode) k_bsc_states<HP, true><<<grid, 256, 0, s>>>(A);
-    else k_bsc_states<HP, false><<<grid, 256, 0, s>>>(A);
+    if (encode) k_bsc_states<HP, true><<<grid, 128, 0, s>>>(A);
+    else k_bsc_states<HP, false><<<grid, 128, 0, s>>>(A);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }
