@@ -104,11 +104,14 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    float rn[8];
+    // per-lane key constants for h = lane + 32 j: the mask keeps the top 24 bits
+    // of the score key, the low byte holds 255 - h; both 0 for an absent latent
+    unsigned kmask[8], klow[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int h = lane + 32 * j;
-        rn[j] = h < H ? rnorm[h] : 0.f;
+        kmask[j] = h < H ? 0xFFFFFF00u : 0u;
+        klow[j] = h < H ? (unsigned)(255 - h) : 0u;
     }
 
     uint32_t phase = 0;
@@ -231,20 +234,26 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 unsigned pk[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int h = lane + 32 * j;
-                    pk[j] = h < H ? (score_key(prow_p[32 * j] * rn[j]) & 0xFFFFFF00u) | (unsigned)(255 - h)
-                                  : 0u;
+                    const float sc = kmask[j] ? prow_p[32 * j] : 0.f;
+                    const unsigned b = __float_as_uint(sc);
+                    // order-preserving key: flip all bits of a negative score,
+                    // only the sign bit of a positive one
+                    const unsigned key = b ^ ((unsigned)((int)b >> 31) | 0x80000000u);
+                    pk[j] = (key & kmask[j]) | klow[j];
                 }
                 sort8_desc(pk);
                 // Hp rounds of the warp maximum; the winning lane pops its head
                 int myh = 0;
-                for (int r = 0; r < Hp; ++r) {
-                    const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
-                    if (lane == r) myh = 255 - (int)(w & 0xFFu);
-                    if (pk[0] == w) {
 #pragma unroll
-                        for (int j = 0; j < 7; ++j) pk[j] = pk[j + 1];
-                        pk[7] = 0u;
+                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                    if (r < Hp) {
+                        const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
+                        if (lane == r) myh = 255 - (int)(w & 0xFFu);
+                        if (pk[0] == w) {
+#pragma unroll
+                            for (int j = 0; j < 7; ++j) pk[j] = pk[j + 1];
+                            pk[7] = 0u;
+                        }
                     }
                 }
                 // FP32 rescore: partial dot products over this lane's d, then a
@@ -310,7 +319,12 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 // this lane now holds the total of round index jr
                 const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
                                ((lane >> 1) & 1);
-                const int rank = topk_rank(myh, Hp, lane);
+                int rank = 0;
+#pragma unroll
+                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                    const int o = __shfl_sync(0xffffffffu, myh, r);
+                    rank += (r < Hp && o < myh) ? 1 : 0;
+                }
                 const int h_jr = __shfl_sync(0xffffffffu, myh, jr & 31);
                 const int rank_jr = __shfl_sync(0xffffffffu, rank, jr & 31);
                 if ((lane & 1) == 0 && jr < Hp) {
@@ -335,16 +349,19 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     }
 }
 
-// BF16 image of W in the operand layout above: K-block kb holds rows h of 128 B
+// BF16 image of the unit-norm rows W_h / ||W_h|| (zero rows stay zero), so that
+// the tensor cores produce the preselection scores directly, in the operand
+// layout above: K-block kb holds rows h of 128 B
 // (d = 64 kb .. 64 kb + 63), 16-byte chunk c stored at chunk position c ^ (h & 7).
-__global__ void k_w_image(const float *__restrict__ Wt, int H, int D, uint16_t *__restrict__ img) {
+__global__ void k_w_image(const float *__restrict__ Wt, const float *__restrict__ rnorm, int H, int D,
+                          uint16_t *__restrict__ img) {
     const int64_t total = (int64_t)H * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int h = (int)(i / D), d = (int)(i % D);
         const int kb = d >> 6, ch = (d & 63) >> 3, w = d & 7;
         const size_t off = (size_t)kb * H * 64 + (size_t)h * 64 + (size_t)((ch ^ (h & 7)) * 8 + w);
-        const __nv_bfloat16 b = __float2bfloat16_rn(Wt[i]);
+        const __nv_bfloat16 b = __float2bfloat16_rn(Wt[i] * rnorm[h]);
         img[off] = *reinterpret_cast<const uint16_t *>(&b);
     }
 }
@@ -359,7 +376,7 @@ size_t bf16_smem_bytes(int D, int H) {
 
 int launch_bsc_bf16_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
     TraceScope tr(c, "bsc_w_image", s);
-    k_w_image<<<c->num_sms * 2, 256, 0, s>>>(W, c->H, c->D, c->Wb);
+    k_w_image<<<c->num_sms * 2, 256, 0, s>>>(W, c->rnorm, c->H, c->D, c->Wb);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }
