@@ -223,15 +223,11 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
             }
             tc_fence_before();
             __syncthreads();
-            for (int i = 0; i < 64 / NW; ++i) {
-                const int p = warp * (64 / NW) + i;
-                const int64_t n = n0 + 64 * half + p;
-                if (n >= N) break;
-                // packed keys: score key rounded down to 24 bits, then 255 - h, so
-                // that one 32-bit maximum ranks by score and breaks ties to the
-                // lower h (H <= 256); 0 marks an absent latent
+            // packed keys: score key rounded down to 24 bits, then 255 - h, so that
+            // one 32-bit maximum ranks by score and breaks ties to the lower h
+            // (H <= 256); 0 marks an absent latent
+            auto make_keys = [&](int p, unsigned (&pk)[8]) {
                 const float *prow_p = Psm + pidx(p, lane, H);   // + 32 j for h = lane + 32 j
-                unsigned pk[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float sc = kmask[j] ? prow_p[32 * j] : 0.f;
@@ -242,95 +238,118 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                     pk[j] = (key & kmask[j]) | klow[j];
                 }
                 sort8_desc(pk);
+            };
+            auto rescore = [&](int64_t n, int myh) {
+                    // FP32 rescore: partial dot products over this lane's d, then a
+                    // transposed warp reduction (16 slots -> one total per lane pair)
+                    float v[16];
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = 0.f;
+                    const float *yrow = Y + n * D;
+                    int hsel[PROSPER_MAX_HPRIME];
+#pragma unroll
+                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
+                        hsel[r] = __shfl_sync(0xffffffffu, myh, r < Hp ? r : 0);
+                    for (int c = lane; c < nchunk; c += 32) {
+                        const float4 y0 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c));
+                        const float4 y1 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c + 4));
+                        // all row loads first (always in bounds), then the dot products
+                        float4 w[2 * PROSPER_MAX_HPRIME];
+#pragma unroll
+                        for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                            const float *wrow = Wt + (size_t)hsel[r] * D + 8 * c;
+                            w[2 * r] = __ldg(reinterpret_cast<const float4 *>(wrow));
+                            w[2 * r + 1] = __ldg(reinterpret_cast<const float4 *>(wrow + 4));
+                        }
+#pragma unroll
+                        for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                            const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
+                            float s = v[r];
+                            s = fmaf(y0.x, w0.x, s); s = fmaf(y0.y, w0.y, s);
+                            s = fmaf(y0.z, w0.z, s); s = fmaf(y0.w, w0.w, s);
+                            s = fmaf(y1.x, w1.x, s); s = fmaf(y1.y, w1.y, s);
+                            s = fmaf(y1.z, w1.z, s); s = fmaf(y1.w, w1.w, s);
+                            v[r] = (r < Hp) ? s : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const bool up = (lane & 16) != 0;
+                        const float send = up ? v[k] : v[k + 8];
+                        const float keep = up ? v[k + 8] : v[k];
+                        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool up = (lane & 8) != 0;
+                        const float send = up ? v[k] : v[k + 4];
+                        const float keep = up ? v[k + 4] : v[k];
+                        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const bool up = (lane & 4) != 0;
+                        const float send = up ? v[k] : v[k + 2];
+                        const float keep = up ? v[k + 2] : v[k];
+                        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    }
+                    {
+                        const bool up = (lane & 2) != 0;
+                        const float send = up ? v[0] : v[1];
+                        const float keep = up ? v[1] : v[0];
+                        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                    }
+                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                    // this lane now holds the total of round index jr
+                    const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                                   ((lane >> 1) & 1);
+                    int rank = 0;
+#pragma unroll
+                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                        const int o = __shfl_sync(0xffffffffu, myh, r);
+                        rank += (r < Hp && o < myh) ? 1 : 0;
+                    }
+                    const int h_jr = __shfl_sync(0xffffffffu, myh, jr & 31);
+                    const int rank_jr = __shfl_sync(0xffffffffu, rank, jr & 31);
+                    if ((lane & 1) == 0 && jr < Hp) {
+                        sel_out[n * SEL_STRIDE + rank_jr] = h_jr;
+                        selp_out[n * SEL_STRIDE + rank_jr] = v[0];
+                    }
+                };
+            // two points at a time, so that the two selections' latency chains
+            // (warp maxima) interleave; then one rescore each
+            for (int i = 0; i < 64 / NW; i += 2) {
+                const int pa = warp * (64 / NW) + i, pb = pa + 1;
+                const int64_t na = n0 + 64 * half + pa, nb = na + 1;
+                if (na >= N) break;
+                unsigned ka[8], kb[8];
+                make_keys(pa, ka);
+                make_keys(pb, kb);
                 // Hp rounds of the warp maximum; the winning lane pops its head
-                int myh = 0;
+                int ha = 0, hb = 0;
 #pragma unroll
                 for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
                     if (r < Hp) {
-                        const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
-                        if (lane == r) myh = 255 - (int)(w & 0xFFu);
-                        if (pk[0] == w) {
+                        const unsigned wa = __reduce_max_sync(0xffffffffu, ka[0]);
+                        const unsigned wb = __reduce_max_sync(0xffffffffu, kb[0]);
+                        if (lane == r) {
+                            ha = 255 - (int)(wa & 0xFFu);
+                            hb = 255 - (int)(wb & 0xFFu);
+                        }
+                        if (ka[0] == wa) {
 #pragma unroll
-                            for (int j = 0; j < 7; ++j) pk[j] = pk[j + 1];
-                            pk[7] = 0u;
+                            for (int j = 0; j < 7; ++j) ka[j] = ka[j + 1];
+                            ka[7] = 0u;
+                        }
+                        if (kb[0] == wb) {
+#pragma unroll
+                            for (int j = 0; j < 7; ++j) kb[j] = kb[j + 1];
+                            kb[7] = 0u;
                         }
                     }
                 }
-                // FP32 rescore: partial dot products over this lane's d, then a
-                // transposed warp reduction (16 slots -> one total per lane pair)
-                float v[16];
-#pragma unroll
-                for (int r = 0; r < 16; ++r) v[r] = 0.f;
-                const float *yrow = Y + n * D;
-                int hsel[PROSPER_MAX_HPRIME];
-#pragma unroll
-                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
-                    hsel[r] = __shfl_sync(0xffffffffu, myh, r < Hp ? r : 0);
-                for (int c = lane; c < nchunk; c += 32) {
-                    const float4 y0 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c));
-                    const float4 y1 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c + 4));
-                    // all row loads first (always in bounds), then the dot products
-                    float4 w[2 * PROSPER_MAX_HPRIME];
-#pragma unroll
-                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                        const float *wrow = Wt + (size_t)hsel[r] * D + 8 * c;
-                        w[2 * r] = __ldg(reinterpret_cast<const float4 *>(wrow));
-                        w[2 * r + 1] = __ldg(reinterpret_cast<const float4 *>(wrow + 4));
-                    }
-#pragma unroll
-                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                        const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
-                        float s = v[r];
-                        s = fmaf(y0.x, w0.x, s); s = fmaf(y0.y, w0.y, s);
-                        s = fmaf(y0.z, w0.z, s); s = fmaf(y0.w, w0.w, s);
-                        s = fmaf(y1.x, w1.x, s); s = fmaf(y1.y, w1.y, s);
-                        s = fmaf(y1.z, w1.z, s); s = fmaf(y1.w, w1.w, s);
-                        v[r] = (r < Hp) ? s : 0.f;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const bool up = (lane & 16) != 0;
-                    const float send = up ? v[k] : v[k + 8];
-                    const float keep = up ? v[k + 8] : v[k];
-                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const bool up = (lane & 8) != 0;
-                    const float send = up ? v[k] : v[k + 4];
-                    const float keep = up ? v[k + 4] : v[k];
-                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-                }
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const bool up = (lane & 4) != 0;
-                    const float send = up ? v[k] : v[k + 2];
-                    const float keep = up ? v[k + 2] : v[k];
-                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                }
-                {
-                    const bool up = (lane & 2) != 0;
-                    const float send = up ? v[0] : v[1];
-                    const float keep = up ? v[1] : v[0];
-                    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-                }
-                v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-                // this lane now holds the total of round index jr
-                const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                               ((lane >> 1) & 1);
-                int rank = 0;
-#pragma unroll
-                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                    const int o = __shfl_sync(0xffffffffu, myh, r);
-                    rank += (r < Hp && o < myh) ? 1 : 0;
-                }
-                const int h_jr = __shfl_sync(0xffffffffu, myh, jr & 31);
-                const int rank_jr = __shfl_sync(0xffffffffu, rank, jr & 31);
-                if ((lane & 1) == 0 && jr < Hp) {
-                    sel_out[n * SEL_STRIDE + rank_jr] = h_jr;
-                    selp_out[n * SEL_STRIDE + rank_jr] = v[0];
-                }
+                rescore(na, ha);
+                if (nb < N) rescore(nb, hb);
             }
             __syncthreads();
         }
