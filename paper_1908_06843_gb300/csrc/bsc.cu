@@ -92,30 +92,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pr
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// Error-free sum of squares of one point's row (double-float: hi + lo), one warp.
-__device__ __forceinline__ float2 warp_sumsq_df(const float *row, int D, int lane) {
-    float hi = 0.f, lo = 0.f;
-    for (int d = lane; d < D; d += 32) {
-        const float v = row[d];
-        const float p = v * v;
-        const float pe = fmaf(v, v, -p);        // exact error of the product
-        const float s = hi + p;                 // TwoSum(hi, p)
-        const float bb = s - hi;
-        lo += ((hi - (s - bb)) + (p - bb)) + pe;
-        hi = s;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        const float s = hi + h2;
-        const float bb = s - hi;
-        lo = lo + l2 + ((hi - (s - bb)) + (h2 - bb));
-        hi = s;
-    }
-    return make_float2(hi, lo);
-}
-
 // Grid: persistent, one 256-thread CTA per SM.  Thread (tp = tid & 7, th = tid >> 3)
 // accumulates the 8 x 8 block P[tp*8 + i][th*8 + j] of the 64 x 256 tile.  The
 // k-chunks of all tiles form one software pipeline: while chunk q is multiplied,
@@ -138,10 +114,13 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
     const int64_t nq = my_tiles * nk;   // chunks this CTA processes
 
     float rn[8];
+    unsigned kmask[8], klow[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int h = lane + 32 * j;
         rn[j] = h < H ? rnorm[h] : 0.f;
+        kmask[j] = h < H ? 0xFFFFFF00u : 0u;
+        klow[j] = h < H ? (unsigned)(255 - h) : 0u;
     }
 
     // Y chunk mapping: thread loads float4 (q4 = idx & 7) of point p = idx >> 3, idx = tid + 256 r
@@ -170,6 +149,8 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
             yreg[r] = v;
         }
     };
+    // partial y^T y of points tid/8 and tid/8 + 32 over this thread's d slices
+    float ysq[2] = {0.f, 0.f};
     auto store_y = [&](int st) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -179,6 +160,10 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
             sm.Ys[st][q4 * 4 + 1][p] = yreg[r].y;
             sm.Ys[st][q4 * 4 + 2][p] = yreg[r].z;
             sm.Ys[st][q4 * 4 + 3][p] = yreg[r].w;
+            float q = ysq[r];
+            q = fmaf(yreg[r].x, yreg[r].x, q); q = fmaf(yreg[r].y, yreg[r].y, q);
+            q = fmaf(yreg[r].z, yreg[r].z, q); q = fmaf(yreg[r].w, yreg[r].w, q);
+            ysq[r] = q;
         }
     };
     auto load_w = [&](int64_t q, int st) {
@@ -247,27 +232,70 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
         }
+        // y^T y of the tile's points: the 8 threads of a point add their slices
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float q = ysq[r];
+            q += __shfl_xor_sync(0xffffffffu, q, 1);
+            q += __shfl_xor_sync(0xffffffffu, q, 2);
+            q += __shfl_xor_sync(0xffffffffu, q, 4);
+            const int64_t n = n0 + (tid >> 3) + 32 * r;
+            if ((tid & 7) == 0 && n < N) {
+                yy_out[n] = make_float2(q, 0.f);
+                if (!isfinite(q)) atomicOr(status, ST_NONFINITE);
+            }
+            ysq[r] = 0.f;
+        }
         __syncthreads();
         for (int i = 0; i < PT / 8; ++i) {
             const int p = warp * (PT / 8) + i;
             const int64_t n = n0 + p;
             if (n >= N) break;
-            unsigned key[8];
+            // H'+1 rounds of the warp maximum over packed keys (24-bit score
+            // prefix, then 255 - h).  When the H'-th and (H'+1)-th winners differ
+            // in the prefix, every latent left out has a smaller exact score than
+            // every one taken, so the set is the exact top-H'; otherwise (scores
+            // within 2^-15 of each other across the boundary, exact ties included)
+            // the exact selection below decides.
+            unsigned pk[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                int h = lane + 32 * j;
-                key[j] = h < H ? score_key(sm.Ps[p][h] * rn[j]) : 0u;
+            for (int j = 0; j < 8; ++j)
+                pk[j] = packed_key(kmask[j] ? sm.Ps[p][lane + 32 * j] * rn[j] : 0.f, kmask[j], klow[j]);
+            sort8_desc(pk);
+            int myh = 0x7fffffff;
+            unsigned wlast = 0u, wnext = 0u;
+#pragma unroll
+            for (int r = 0; r <= PROSPER_MAX_HPRIME; ++r) {
+                if (r <= Hp) {
+                    const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
+                    if (lane == r && r < Hp) myh = 255 - (int)(w & 0xFFu);
+                    if (r == Hp - 1) wlast = w;
+                    if (r == Hp) wnext = w;
+                    if (pk[0] == w) {
+#pragma unroll
+                        for (int j = 0; j < 7; ++j) pk[j] = pk[j + 1];
+                        pk[7] = 0u;
+                    }
+                }
             }
-            const int myh = warp_topk(key, Hp, lane, sm.topk[warp]);
-            const int rank = topk_rank(myh, Hp, lane);
+            if (Hp < H && (wlast >> 8) == (wnext >> 8)) {
+                unsigned key[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    int h = lane + 32 * j;
+                    key[j] = h < H ? score_key(sm.Ps[p][h] * rn[j]) : 0u;
+                }
+                myh = warp_topk(key, Hp, lane, sm.topk[warp]);
+            }
+            int rank = 0;
+#pragma unroll
+            for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+                const int o = __shfl_sync(0xffffffffu, myh, r);
+                rank += (r < Hp && o < myh) ? 1 : 0;
+            }
             if (lane < Hp) {
                 sel_out[n * SEL_STRIDE + rank] = myh;
                 selp_out[n * SEL_STRIDE + rank] = sm.Ps[p][myh];
-            }
-            const float2 yy = warp_sumsq_df(Y + n * D, D, lane);
-            if (lane == 0) {
-                yy_out[n] = yy;
-                if (!isfinite(yy.x)) atomicOr(status, ST_NONFINITE);
             }
         }
         __syncthreads();

@@ -41,18 +41,6 @@ __device__ __forceinline__ int pidx(int row, int col, int H) {
     return row * H + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
 }
 
-// descending sort of 8 keys: Batcher's odd-even merge network (19 comparators)
-__device__ __forceinline__ void sort8_desc(unsigned (&k)[8]) {
-#define PROSPER_CE(i, j) { const unsigned a = max(k[i], k[j]), b = min(k[i], k[j]); k[i] = a; k[j] = b; }
-    PROSPER_CE(0, 1) PROSPER_CE(2, 3) PROSPER_CE(4, 5) PROSPER_CE(6, 7)
-    PROSPER_CE(0, 2) PROSPER_CE(1, 3) PROSPER_CE(4, 6) PROSPER_CE(5, 7)
-    PROSPER_CE(1, 2) PROSPER_CE(5, 6)
-    PROSPER_CE(0, 4) PROSPER_CE(1, 5) PROSPER_CE(2, 6) PROSPER_CE(3, 7)
-    PROSPER_CE(2, 4) PROSPER_CE(3, 5)
-    PROSPER_CE(1, 2) PROSPER_CE(3, 4) PROSPER_CE(5, 6)
-#undef PROSPER_CE
-}
-
 // byte offset of the 16-byte chunk c (8 BF16 values, d = 8c .. 8c+7) of row r in a
 // K-major 128-byte-swizzled operand with `rows` rows per 64-wide K-block
 __device__ __forceinline__ uint32_t opnd_off(int r, int c, int rows) {
@@ -229,14 +217,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
             auto make_keys = [&](int p, unsigned (&pk)[8]) {
                 const float *prow_p = Psm + pidx(p, lane, H);   // + 32 j for h = lane + 32 j
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float sc = kmask[j] ? prow_p[32 * j] : 0.f;
-                    const unsigned b = __float_as_uint(sc);
-                    // order-preserving key: flip all bits of a negative score,
-                    // only the sign bit of a positive one
-                    const unsigned key = b ^ ((unsigned)((int)b >> 31) | 0x80000000u);
-                    pk[j] = (key & kmask[j]) | klow[j];
-                }
+                for (int j = 0; j < 8; ++j) pk[j] = packed_key(kmask[j] ? prow_p[32 * j] : 0.f, kmask[j], klow[j]);
                 sort8_desc(pk);
             };
             auto rescore = [&](int64_t n, int myh) {

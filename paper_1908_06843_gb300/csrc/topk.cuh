@@ -101,6 +101,30 @@ __device__ __forceinline__ int warp_topk(unsigned (&key)[8], int Hp, int lane,
     return lane < Hp ? chh : 0x7fffffff;
 }
 
+// descending sort of 8 keys: Batcher's odd-even merge network (19 comparators)
+__device__ __forceinline__ void sort8_desc(unsigned (&k)[8]) {
+#define PROSPER_CE(i, j) { const unsigned a = max(k[i], k[j]), b = min(k[i], k[j]); k[i] = a; k[j] = b; }
+    PROSPER_CE(0, 1) PROSPER_CE(2, 3) PROSPER_CE(4, 5) PROSPER_CE(6, 7)
+    PROSPER_CE(0, 2) PROSPER_CE(1, 3) PROSPER_CE(4, 6) PROSPER_CE(5, 7)
+    PROSPER_CE(1, 2) PROSPER_CE(5, 6)
+    PROSPER_CE(0, 4) PROSPER_CE(1, 5) PROSPER_CE(2, 6) PROSPER_CE(3, 7)
+    PROSPER_CE(2, 4) PROSPER_CE(3, 5)
+    PROSPER_CE(1, 2) PROSPER_CE(3, 4) PROSPER_CE(5, 6)
+#undef PROSPER_CE
+}
+
+// Packed preselection key of score s for latent h (H <= 256): the
+// order-preserving key of s rounded down to its top 24 bits, with 255 - h in
+// the low byte, so that one 32-bit comparison ranks by score and breaks ties
+// (exact ones and those the rounding makes) to the lower h.  kmask / klow are
+// 0xFFFFFF00 / 255 - h for a present latent and 0 / 0 for an absent one.
+__device__ __forceinline__ unsigned packed_key(float s, unsigned kmask, unsigned klow) {
+    const unsigned b = __float_as_uint(s);
+    // flip all bits of a negative score, only the sign bit of a positive one
+    const unsigned key = b ^ ((unsigned)((int)b >> 31) | 0x80000000u);
+    return (key & kmask) | klow;
+}
+
 // Rank of this lane's selected h among the Hp selected ones (ascending h).
 __device__ __forceinline__ int topk_rank(int myh, int Hp, int lane) {
     int rank = 0;
