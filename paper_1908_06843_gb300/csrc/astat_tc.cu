@@ -306,15 +306,34 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
     }
 }
 
-// At += sum over the per-CTA partials, in FP64 and in CTA order
+// FP32 -> FP64 from the IEEE-754 fields on the integer pipe (exact for normal
+// floats, subnormals to 0): the FP64 pipe of this part is too slow for one
+// conversion per element.
+__device__ __forceinline__ double widen(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned m = (e == 0u) ? 0u : (u & 0x7FFFFFu);
+    const unsigned e64 = (e == 0u) ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
+    return __hiloint2double((int)((u & 0x80000000u) | (e64 << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// At += sum over the per-CTA partials in CTA order.  The sum is carried as an
+// unevaluated FP32 pair hi + lo (Knuth's TwoSum per addition, error about
+// 2^-44 relative) on the FP32 pipe and widened to FP64 once at the end.
 __global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int64_t HD,
                                double *__restrict__ At) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < HD;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
+        float hi = 0.f, lo = 0.f;
 #pragma unroll 8
-        for (int p = 0; p < nparts; ++p) s += (double)__ldg(part + (size_t)p * HD + i);
-        At[i] += s;
+        for (int p = 0; p < nparts; ++p) {
+            const float b = __ldg(part + (size_t)p * HD + i);
+            const float s = hi + b;
+            const float bb = s - hi;
+            lo += (hi - (s - bb)) + (b - bb);
+            hi = s;
+        }
+        At[i] += widen(hi) + widen(lo);
     }
 }
 
