@@ -422,18 +422,20 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     // per-call constants, formed once per CTA (FP64 logs and divisions are
     // slow on this part):  lpi = log2e log(pi/(1-pi)),  is2 = log2e / sigma^2,
     // log p(y, s=0) = c0 - y^T y / (2 sigma^2)
+    // (the FP64 chains run in lane 0 of four different warps, i.e. on four
+    // SM sub-partitions, while every thread loads its candidate list and G block)
     __shared__ float s_lpi, s_is2;
     __shared__ double s_c0, s_inv2s2;
-    if (threadIdx.x == 0) {
+    if ((threadIdx.x & 31) == 0) {
         const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
         const double s2 = sigma * sigma;
-        s_lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634);
-        s_is2 = (float)(1.4426950408889634 / s2);
-        s_c0 = A.H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2));
-        s_inv2s2 = 0.5 / s2;
+        switch (threadIdx.x >> 5) {
+            case 0: s_lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634); break;
+            case 1: s_is2 = (float)(1.4426950408889634 / s2); break;
+            case 2: s_c0 = A.H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2)); break;
+            default: s_inv2s2 = 0.5 / s2; break;
+        }
     }
-    __syncthreads();
-    const float lpi = s_lpi, is2 = s_is2;
     const int gamma = A.gamma;
     const int H = A.H;
 
@@ -459,11 +461,18 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
                 }
         }
     }
+    float g[HP][HP];
+#pragma unroll
+    for (int i = 0; i < HP; ++i)
+#pragma unroll
+        for (int j = i; j < HP; ++j) g[i][j] = __ldg(A.G + (size_t)I[i] * H + I[j]);
+    __syncthreads();
+    const float lpi = s_lpi, is2 = s_is2;
     float a[HP], b[HP][HP];
 #pragma unroll
     for (int j = 0; j < HP; ++j) {
         float pj = P[j];
-        float gjj = __ldg(A.G + (size_t)I[j] * H + I[j]);
+        float gjj = g[j][j];
         a[j] = lpi + (pj - 0.5f * gjj) * is2;
         b[j][j] = 0.f;
     }
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     for (int i = 0; i < HP; ++i)
 #pragma unroll
         for (int j = i + 1; j < HP; ++j) {
-            b[i][j] = -__ldg(A.G + (size_t)I[i] * H + I[j]) * is2;
+            b[i][j] = -g[i][j] * is2;
             b[j][i] = b[i][j];
         }
 
