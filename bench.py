@@ -337,6 +337,46 @@ def serve_sweep(torch, Y, Wt, rates=(1e2, 1e3, 1e4, 3e4, 1e5), seconds=1.0):
             "latency": "library-side submit -> completion observed by the scheduler"}
 
 
+def secondary_configs(torch, dev, steps, warmup):
+    """E-step (and M-step) throughput of the other two model rows on their own
+    workloads: MCA max-superposition bars (D=100, H=20, H'=8, gamma=4, 163 states,
+    N=100,000) and GSC spike-and-slab (D=64, H=32, H'=8, gamma=3, 93 states,
+    N=50,000), at the generating parameters (MCA W shifted by 0.05 > 0)."""
+    from paper_1908_06843_gb300 import FP32, GSC, MCA, Context, synth
+    out = {}
+    cases = [
+        ("mca_bars", MCA, synth.mca_bars(N=100_000, seed=1003), 8, 4, 0.1, 1.0, 20.0,
+         "MCA bars D=100 H=20 H'=8 gamma=4 (163 states) N=100000, FP32"),
+        ("gsc", GSC, synth.gsc(N=50_000, seed=1004), 8, 3, 3.0 / 32.0, 0.3, 0.0,
+         "GSC D=64 H=32 H'=8 gamma=3 (93 states) N=50000, FP32 states + FP64 subset table"),
+    ]
+    for name, model, d, hp, gamma, pi, sigma, rho, label in cases:
+        try:
+            Y = np.asarray(d["Y"], np.float32)
+            Wt = np.asarray(d["Wt"] + (0.05 if model == MCA else 0.0), np.float32)
+            n, dd = Y.shape
+            hh = Wt.shape[0]
+            ctx = Context(model, dd, hh, hp, gamma, FP32, max_points=n)
+            W = torch.tensor(Wt, device=dev)
+            theta = torch.tensor([pi, sigma, rho, 0.0], dtype=torch.float64, device=dev)
+            mu = psi = None
+            if model == GSC:
+                mu = torch.tensor(np.asarray(d["mu"], np.float32), device=dev)
+                psi = torch.tensor(np.asarray(d["psi"], np.float32), device=dev)
+            P = ctx.params(W, theta, mu, psi)
+            Yg = torch.tensor(Y, device=dev)
+            st = ctx.alloc_stats()
+            ms, kern, _ = bench_form(torch, ctx, P, Yg, st, steps, warmup, None, None)
+            per = {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps} for k, v in kern.items()}
+            out[name] = {"workload": label, "value": n * steps / (ms * 1e-3), "unit": "points/s",
+                         "ms_per_step": ms / steps, "kernels": per,
+                         "F_per_point": float(st["scal"][0].item()) / n}
+            ctx.close()
+        except Exception as e:    # reported, not hidden
+            out[name] = {"error": str(e)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,6 +389,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--points", type=int, default=NPTS, help="points per GPU (profiling cases)")
     ap.add_argument("--form", default="both", choices=["both", "bf16_rescore", "fp32"])
+    ap.add_argument("--no-secondary", action="store_true", help="skip the MCA and GSC workloads")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -452,6 +493,9 @@ def main():
             serving = serve_sweep(torch, Y, Wt)
         except Exception as e:    # reported, not hidden
             serving = {"error": str(e)}
+    secondary = None
+    if not args.no_secondary and args.form == "both" and args.points == NPTS:
+        secondary = secondary_configs(torch, dev, args.steps, args.warmup)
     head_name = "bf16_rescore" if "value" in forms.get("bf16_rescore", {}) else "fp32"
     head = forms[head_name]
     cpu = None
@@ -469,7 +513,7 @@ def main():
                    "parallelism": f"weak x{ws}, no data-path collective"},
         "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"],
         "clocks": head["clocks"], "gpu_launches": int(round(head["gpu_launches_per_step"] * args.steps)),
-        "forms": forms, "serving": serving,
+        "forms": forms, "serving": serving, "secondary": secondary,
     }
     print(json.dumps(out), flush=True)
     if dist is not None:

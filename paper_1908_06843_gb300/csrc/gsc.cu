@@ -121,6 +121,13 @@ __device__ __forceinline__ float fast_ex2(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// acc (hi, lo) += v with Knuth's TwoSum (hi + lo carries about 48 bits)
+__device__ __forceinline__ void two_sum_acc(float2 &acc, float v) {
+    const float s = acc.x + v;
+    const float bb = s - acc.x;
+    acc.y += (acc.x - (s - bb)) + (v - bb);
+    acc.x = s;
+}
 __device__ __forceinline__ float wsum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -141,7 +148,7 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
     extern __shared__ __align__(16) float sm[];
     const int D = A.D, H = A.H, gamma = A.gamma, nK = A.nK;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *Ws = sm;                                  // H x D
+    float *Ws = sm;                                  // D x H (transposed: lane h reads row d)
     float *Gs = Ws + H * D;                          // H x H
     unsigned *Ks = reinterpret_cast<unsigned *>(Gs + H * H);   // nK canonical masks
     float *wbase = reinterpret_cast<float *>(Ks + ((nK + 3) & ~3));
@@ -150,7 +157,8 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
     float *gpart = acc + S::N * 32 + 64;             // 3H
     float *apart = gpart + 3 * H;                    // H x D
 
-    for (int i = tid; i < H * D; i += GW * 32) Ws[i] = A.W[i];
+    for (int i = tid; i < H * D; i += GW * 32) Ws[(i % D) * H + i / D] = A.W[i];
+    float *ysm = wbase + (size_t)GW * (S::N * 32 + 64 + 3 * H + H * D) + (size_t)warp * D;   // per warp
     for (int i = tid; i < H * H; i += GW * 32) Gs[i] = A.G[i];
     if (tid == 0) {   // canonical state masks: by size, then lexicographic
         int n = 0;
@@ -180,7 +188,11 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
     const float is2 = (float)(1.0 / (sigma * sigma));
     const float is4 = is2 * is2;
     const double logp00 = H * log(1.0 - pi) - 0.5 * D * (kLog2Pi + log(sigma * sigma));
-    double accF = 0.0, accS1 = 0.0, accYY = 0.0, accN = 0.0;
+    const double i2s2 = 0.5 / (sigma * sigma);
+    // per-warp sums of F, sum<|s|> and y^T y as FP32 pairs (hi + lo, Knuth's
+    // TwoSum): FP64 adds are ~65x slower than FP32 ones on this part
+    float2 accF = make_float2(0.f, 0.f), accS1 = accF, accYY = accF;
+    int accN = 0;
 
     const int64_t gw = (int64_t)blockIdx.x * GW + warp, nw = (int64_t)gridDim.x * GW;
     for (int64_t n = gw; n < A.N; n += nw) {
@@ -194,18 +206,26 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 #pragma unroll
         for (int k = 0; k < DK; ++k) yy = fmaf(y[k], y[k], yy);
         yy = wsum(yy);
-        // projections p_h (lane h holds p_h; H <= 32)
-        float ph = 0.f;
-        for (int h = 0; h < H; ++h) {
-            float p = 0.f;
+        // projections p_h: lane h forms W_h . y from the transposed dictionary
+        // and the point's y staged in this warp's shared buffer (H <= 32)
 #pragma unroll
-            for (int k = 0; k < DK; ++k) {
-                const int d = lane + 32 * k;
-                if (d < D) p = fmaf(Ws[h * D + d], y[k], p);
-            }
-            p = wsum(p);
-            if (lane == h) ph = p;
+        for (int k = 0; k < DK; ++k) {
+            const int d = lane + 32 * k;
+            if (d < D) ysm[d] = y[k];
         }
+        __syncwarp();
+        float ph = 0.f;
+        if (lane < H) {
+            float p0 = 0.f, p1 = 0.f;
+            int d = 0;
+            for (; d + 1 < D; d += 2) {
+                p0 = fmaf(Ws[d * H + lane], ysm[d], p0);
+                p1 = fmaf(Ws[(d + 1) * H + lane], ysm[d + 1], p1);
+            }
+            if (d < D) p0 = fmaf(Ws[d * H + lane], ysm[d], p0);
+            ph = p0 + p1;
+        }
+        __syncwarp();
         // singleton log-joint (terms common to all h dropped) as the selection score
         unsigned key[8];
 #pragma unroll
@@ -356,7 +376,7 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
             acc[o * 32] = s * invZ;         // slot o, column 0 now holds the normalised value
         }
         __syncwarp();
-        const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp00 - (double)yy * 0.5 / (sigma * sigma);
+        const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp00 - (double)yy * i2s2;
         if (ENCODE) {
             if (lane == 0) {
                 if (A.sel_out)
@@ -405,18 +425,20 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
         }
         __syncwarp();
         if (lane == 0) {
-            accF += logZ;
-            accS1 += (double)s1;
-            accYY += (double)yy;
-            accN += 1.0;
+            const float fh = (float)logZ;
+            two_sum_acc(accF, fh);
+            two_sum_acc(accF, (float)(logZ - (double)fh));
+            two_sum_acc(accS1, s1);
+            two_sum_acc(accYY, yy);
+            ++accN;
         }
     }
     if (ENCODE) return;
     if (lane == 0) {
-        atomicAdd(A.scal + PROSPER_SC_F, accF);
-        atomicAdd(A.scal + PROSPER_SC_S1, accS1);
-        atomicAdd(A.scal + PROSPER_SC_YY, accYY);
-        atomicAdd(A.scal + PROSPER_SC_N, accN);
+        atomicAdd(A.scal + PROSPER_SC_F, (double)accF.x + (double)accF.y);
+        atomicAdd(A.scal + PROSPER_SC_S1, (double)accS1.x + (double)accS1.y);
+        atomicAdd(A.scal + PROSPER_SC_YY, (double)accYY.x + (double)accYY.y);
+        atomicAdd(A.scal + PROSPER_SC_N, (double)accN);
     }
     __syncthreads();
     const int stride = S::N * 32 + 64 + 3 * H + H * D;
@@ -434,6 +456,7 @@ size_t gsc_smem(int D, int H, int nK) {
     using S = Slots<HP>;
     size_t f = (size_t)H * D + (size_t)H * H + ((nK + 3) & ~3);
     f += (size_t)GW * (S::N * 32 + 64 + 3 * H + H * D);
+    f += (size_t)GW * D;   // per-warp y buffers
     return f * sizeof(float);
 }
 

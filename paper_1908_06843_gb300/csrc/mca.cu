@@ -61,8 +61,16 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// shared layout: W (H x D), log2 W (H x D), 1/sum_d W_dh (H), per warp
+// shared layout: W (H x D), log2 W (H x D), W transposed (D x H), 1/sum_d W_dh (H), per warp
 // { l[KMAX], mask[KMAX] } and, with SMEM_STATS, per warp sum<A>y and sum<A> (H x D each)
+// acc (hi, lo) += v with Knuth's TwoSum (hi + lo carries about 48 bits)
+__device__ __forceinline__ void two_sum_acc(float2 &acc, float v) {
+    const float s = acc.x + v;
+    const float bb = s - acc.x;
+    acc.y += (acc.x - (s - bb)) + (v - bb);
+    acc.x = s;
+}
+
 constexpr int KMAX = 1024;
 
 template <int DK, bool ENCODE, bool SMEM_STATS>
@@ -71,7 +79,8 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
     const int D = A.D, H = A.H, Hp = A.Hp, gamma = A.gamma;
     float *Ws = sm;
     float *Ls = Ws + H * D;
-    float *Rc = Ls + H * D;
+    float *WsT = Ls + H * D;             // D x H: lane h reads row d (preselection)
+    float *Rc = WsT + H * D;
     float *wl = Rc + ((H + 3) & ~3);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *ell = wl + warp * 2 * KMAX;
@@ -82,6 +91,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
     for (int i = tid; i < H * D; i += MW * 32) {
         const float w = A.W[i];
         Ws[i] = w;
+        WsT[(i % D) * H + i / D] = w;
         Ls[i] = w > 0.f ? log2f(w) : -INFINITY;
     }
     for (int h = tid; h < H; h += MW * 32) {
@@ -98,8 +108,12 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
     const float lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634);
     const float ih = (float)(1.4426950408889634 / (2.0 * sigma * sigma));   // log2e / (2 sigma^2)
     const double logp00 = H * log(1.0 - pi) - 0.5 * D * (kLog2Pi + log(sigma * sigma));
+    const double i2s2 = 0.5 / (sigma * sigma);
 
-    double accF = 0.0, accS1 = 0.0, accYY = 0.0, accR2 = 0.0, accN = 0.0;
+    // per-warp sums as FP32 pairs (hi + lo, Knuth's TwoSum): FP64 adds are
+    // ~65x slower than FP32 ones on this part
+    float2 accF = make_float2(0.f, 0.f), accS1 = accF, accYY = accF, accR2 = accF;
+    int accN = 0;
     const int64_t gw = (int64_t)blockIdx.x * MW + warp, nw = (int64_t)gridDim.x * MW;
     for (int64_t n = gw; n < A.N; n += nw) {
         float y[DK];
@@ -112,27 +126,32 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
         for (int k = 0; k < DK; ++k) yy = fmaf(y[k], y[k], yy);
         yy = warp_sum(yy);
-        // ---- preselection: lane h gets sum_d W_dh y_d (H <= 256: 8 per lane)
+        // ---- preselection: lane h gets sum_d W_dh y_d (H <= 256: 8 per lane) from
+        //      the transposed dictionary and the point's y staged in the warp's
+        //      state buffer (free until pass 1)
+#pragma unroll
+        for (int k = 0; k < DK; ++k) {
+            const int d = lane + 32 * k;
+            if (d < D) ell[d] = y[k];
+        }
+        __syncwarp();
         unsigned key[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) key[j] = 0u;
-        for (int h0 = 0; h0 < H; h0 += 32) {
-            float mine = 0.f;
-            for (int hh = 0; hh < 32 && h0 + hh < H; ++hh) {
-                float p = 0.f;
-#pragma unroll
-                for (int k = 0; k < DK; ++k) {
-                    const int d = lane + 32 * k;
-                    if (d < D) p = fmaf(Ws[(h0 + hh) * D + d], y[k], p);
+        for (int j = 0; j < 8; ++j) {
+            const int h = lane + 32 * j;
+            key[j] = 0u;
+            if (h < H) {
+                float p0 = 0.f, p1 = 0.f;
+                int d = 0;
+                for (; d + 1 < D; d += 2) {
+                    p0 = fmaf(WsT[d * H + h], ell[d], p0);
+                    p1 = fmaf(WsT[(d + 1) * H + h], ell[d + 1], p1);
                 }
-                p = warp_sum(p);
-                if (lane == hh) mine = p;
+                if (d < D) p0 = fmaf(WsT[d * H + h], ell[d], p0);
+                key[j] = score_key((p0 + p1) * Rc[h]);
             }
-            const int h = h0 + lane;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (j == (h0 >> 5) && h < H) key[j] = score_key(mine * Rc[h]);
         }
+        __syncwarp();
         const int myh = warp_topk(key, Hp, lane, msk);   // msk doubles as scratch here
         __syncwarp();
         const int rank = topk_rank(myh, Hp, lane);
@@ -265,8 +284,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
         for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) es[j] = warp_sum(es[j]);
         best = __reduce_min_sync(0xffffffffu, (unsigned)best);
         const float invZ = 1.f / Z;
-        const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp00 -
-                            (double)yy / (2.0 * sigma * sigma);
+        const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp00 - (double)yy * i2s2;
 
         if (ENCODE) {
             if (lane == 0) {
@@ -339,20 +357,22 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
             }
         }
         if (lane == 0) {
-            accF += logZ;
-            accS1 += (double)(S1 * invZ);
-            accYY += (double)yy;
-            accR2 += (double)R2;
-            accN += 1.0;
+            const float fh = (float)logZ;
+            two_sum_acc(accF, fh);
+            two_sum_acc(accF, (float)(logZ - (double)fh));
+            two_sum_acc(accS1, S1 * invZ);
+            two_sum_acc(accYY, yy);
+            two_sum_acc(accR2, R2);
+            ++accN;
         }
     }
     if (ENCODE) return;
     if (lane == 0) {
-        atomicAdd(A.scal + PROSPER_SC_F, accF);
-        atomicAdd(A.scal + PROSPER_SC_S1, accS1);
-        atomicAdd(A.scal + PROSPER_SC_YY, accYY);
-        atomicAdd(A.scal + PROSPER_SC_MCA_R2, accR2);
-        atomicAdd(A.scal + PROSPER_SC_N, accN);
+        atomicAdd(A.scal + PROSPER_SC_F, (double)accF.x + (double)accF.y);
+        atomicAdd(A.scal + PROSPER_SC_S1, (double)accS1.x + (double)accS1.y);
+        atomicAdd(A.scal + PROSPER_SC_YY, (double)accYY.x + (double)accYY.y);
+        atomicAdd(A.scal + PROSPER_SC_MCA_R2, (double)accR2.x + (double)accR2.y);
+        atomicAdd(A.scal + PROSPER_SC_N, (double)accN);
     }
     if (SMEM_STATS) {
         __syncthreads();
@@ -366,7 +386,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 }
 
 size_t mca_smem(int D, int H, bool smem_stats) {
-    size_t f = 2 * (size_t)H * D + ((H + 3) & ~3) + (size_t)MW * 2 * KMAX;
+    size_t f = 3 * (size_t)H * D + ((H + 3) & ~3) + (size_t)MW * 2 * KMAX;
     if (smem_stats) f += (size_t)MW * 2 * H * D;
     return f * sizeof(float);
 }
