@@ -33,6 +33,12 @@ __host__ __device__ inline int64_t binom_small(int n, int k) {
     for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
     return r;
 }
+// C(n, k) for k <= 3 without division loops (64-bit integer division is a
+// long software sequence on the GPU; this runs for every state of every point)
+__device__ __forceinline__ int binom3(int n, int k) {
+    if (n < k) return 0;
+    return k == 0 ? 1 : k == 1 ? n : k == 2 ? n * (n - 1) / 2 : n * (n - 1) * (n - 2) / 6;
+}
 // first index of the size-k block (blocks ordered by size, colex inside)
 __host__ __device__ inline int64_t sub_offset(int H, int k) {
     int64_t o = 0;
@@ -266,10 +272,10 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 #pragma unroll
                     for (int j = 0; j < HP; ++j)
                         if (((mk >> j) & 1u) && q < 3) { bl[q] = j; bg[q] = I[j]; ++q; }
-                    int64_t rk = sub_offset(H, k);
+                    int rk = (k > 1 ? H : 0) + (k > 2 ? H * (H - 1) / 2 : 0);   // first index of the size-k block
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
-                        if (i < k) rk += binom_small(bg[i], i + 1);
+                        if (i < k) rk += binom3(bg[i], i + 1);
                     const float *t = A.tab + rk * TAB;
                     float mi[3][3];
                     mi[0][0] = t[1]; mi[0][1] = mi[1][0] = t[2]; mi[0][2] = mi[2][0] = t[3];
@@ -327,10 +333,10 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 #pragma unroll
             for (int j = 0; j < HP; ++j)
                 if (((mk >> j) & 1u) && q < 3) { bl[q] = j; bg[q] = I[j]; ++q; }
-            int64_t rk = sub_offset(H, k);
+            int rk = (k > 1 ? H : 0) + (k > 2 ? H * (H - 1) / 2 : 0);   // first index of the size-k block
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                if (i < k) rk += binom_small(bg[i], i + 1);
+                if (i < k) rk += binom3(bg[i], i + 1);
             const float *t = A.tab + rk * TAB;
             float mi[3][3];
             mi[0][0] = t[1]; mi[0][1] = mi[1][0] = t[2]; mi[0][2] = mi[2][0] = t[3];

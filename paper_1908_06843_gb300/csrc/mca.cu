@@ -324,19 +324,23 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
             for (int k = 0; k < DK; ++k) {
                 const int d = lane + 32 * k;
                 if (d >= D) continue;
+                // log2 W_dh of the state's active units, read once
+                float lw[PROSPER_MAX_HPRIME];
                 float lmax = -INFINITY;
 #pragma unroll
-                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
-                    if ((mk >> j) & 1u) lmax = fmaxf(lmax, Ls[I[j] * D + d]);
+                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+                    lw[j] = ((mk >> j) & 1u) ? Ls[I[j] * D + d] : -INFINITY;
+                    lmax = fmaxf(lmax, lw[j]);
+                }
                 float t = 0.f;
 #pragma unroll
                 for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
-                    if ((mk >> j) & 1u) t += fast_ex2(rho * (Ls[I[j] * D + d] - lmax));
+                    if ((mk >> j) & 1u) t += fast_ex2(rho * (lw[j] - lmax));
                 const float lbar = lmax + fast_lg2(t) / rho;     // log2 Wbar_d(s)
 #pragma unroll
                 for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
                     if ((mk >> j) & 1u)
-                        Abar[j][k] = fmaf(q, fast_ex2((rho - 1.f) * (Ls[I[j] * D + d] - lbar)), Abar[j][k]);
+                        Abar[j][k] = fmaf(q, fast_ex2((rho - 1.f) * (lw[j] - lbar)), Abar[j][k]);
             }
         }
 #pragma unroll
