@@ -453,9 +453,10 @@ def main():
         e2e = None
         if not args.no_e2e:
             Yh = torch.from_numpy(Y).pin_memory()
-            At_h = np.zeros((H, D))
-            B_h = np.zeros((H, H))
-            sc_h = np.zeros(8)
+            # pinned host buffers for the statistics read back each step
+            At_h = torch.zeros((H, D), dtype=torch.float64).pin_memory()
+            B_h = torch.zeros((H, H), dtype=torch.float64).pin_memory()
+            sc_h = torch.zeros(8, dtype=torch.float64).pin_memory()
             for _ in range(2):
                 ctx.estep_host(P, Yh, At_h, B_h, sc_h)
             e2e_steps = max(3, min(args.steps, 20))

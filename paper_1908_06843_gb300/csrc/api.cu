@@ -101,6 +101,7 @@ static int check_stats(const prosper_ctx *c, const prosper_stats *st) {
 static int estep_begin(prosper_ctx *c, const prosper_params *p, prosper_stats *st,
                        cudaStream_t s) {
     const size_t H = c->H, D = c->D;
+    c->apart_pieces = 0;
     PROSPER_CUDA_TRY(cudaMemsetAsync(st->At, 0, sizeof(double) * H * D, s));
     PROSPER_CUDA_TRY(cudaMemsetAsync(st->B, 0, sizeof(double) * H * H, s));
     PROSPER_CUDA_TRY(cudaMemsetAsync(st->scal, 0, sizeof(double) * PROSPER_SC_LEN, s));
@@ -131,6 +132,8 @@ static int estep_piece(prosper_ctx *c, const prosper_params *p, const float *Y, 
 }
 
 static int estep_end(prosper_ctx *c, prosper_stats *st, cudaStream_t s) {
+    int rc = finish_astat_tc(c, st->At, s);
+    if (rc) return rc;
     return launch_symmetrize(c, st->B, s);
 }
 
@@ -302,6 +305,12 @@ int prosper_destroy(prosper_ctx *c) {
     cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
     cudaFree(c->mca_logW); cudaFree(c->gsc_tab);
     cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es); cudaFree(c->apart);
+    if (c->h_copy) {
+        cudaStreamSynchronize(c->h_copy);
+        for (int i = 0; i < 3; ++i) { cudaEventDestroy(c->h_copied[i]); cudaEventDestroy(c->h_used[i]); }
+        cudaEventDestroy(c->h_start);
+        cudaStreamDestroy(c->h_copy);
+    }
     cudaFree(c->mB); cudaFree(c->mX); cudaFree(c->mI); cudaFree(c->mP); cudaFree(c->mY); cudaFree(c->mZ); cudaFree(c->mW); cudaFree(c->mpart); cudaFree(c->d_status);
     cudaFree(c->d_stage);
     if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -373,13 +382,25 @@ int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_h
     if (rc) return rc;
     if (N < 0 || (N > 0 && !Y_host)) { set_error("bad Y/N"); return PROSPER_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
+    // pieces of 32,768 points (32 MB at D = 256) through NSTAGE device staging
+    // buffers: the host link (about 210 GB/s on this part) moves a piece in
+    // ~160 us, longer than its E-step work, so the copies run back to back
+    // (smaller pieces leave the kernels too little work to fill the GPU)
+    constexpr int NSTAGE = 3;
     const int64_t piece = std::min<int64_t>(c->chunk, 32768);
     const size_t H = c->H, D = c->D;
     if (!c->d_stage) {
-        // two device staging buffers + the device statistics of this call
-        size_t bytes = sizeof(float) * 2 * (size_t)piece * D;
+        size_t bytes = sizeof(float) * NSTAGE * (size_t)piece * D;
         PROSPER_CUDA_TRY(cudaMalloc(&c->d_stage, bytes));
         c->stage_points = piece;
+    }
+    if (!c->h_copy) {
+        PROSPER_CUDA_TRY(cudaStreamCreateWithFlags(&c->h_copy, cudaStreamNonBlocking));
+        for (int i = 0; i < NSTAGE; ++i) {
+            PROSPER_CUDA_TRY(cudaEventCreateWithFlags(&c->h_copied[i], cudaEventDisableTiming));
+            PROSPER_CUDA_TRY(cudaEventCreateWithFlags(&c->h_used[i], cudaEventDisableTiming));
+        }
+        PROSPER_CUDA_TRY(cudaEventCreateWithFlags(&c->h_start, cudaEventDisableTiming));
     }
     const size_t need = H * D + H * H + PROSPER_SC_LEN + 3 * H + 2 * H * D;
     if (!c->d_hstats) PROSPER_CUDA_TRY(cudaMalloc(&c->d_hstats, sizeof(double) * need));
@@ -389,34 +410,28 @@ int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_h
     st.scal = st.B + H * H;
     st.gsc = st.scal + PROSPER_SC_LEN;
     st.mca = st.gsc + 3 * H;
+    cudaStream_t cs = c->h_copy;
+    // the copy stream starts after the work queued on s before this call (the
+    // staging buffers are then free), in parallel with the E-step's prologue
+    cudaEventRecord(c->h_start, s);
+    cudaStreamWaitEvent(cs, c->h_start, 0);
     if ((rc = estep_begin(c, p, &st, s))) return rc;
-    cudaStream_t cs;
-    PROSPER_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaEvent_t copied[2], used[2];
-    for (int i = 0; i < 2; ++i) {
-        cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
-        cudaEventCreateWithFlags(&used[i], cudaEventDisableTiming);
-    }
-    // the copy stream starts after everything queued so far on s
-    cudaEvent_t start;
-    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
-    cudaEventRecord(start, s);
-    cudaStreamWaitEvent(cs, start, 0);
     int k = 0;
     for (int64_t n0 = 0; n0 < N && !rc; n0 += piece, ++k) {
         const int64_t n = std::min<int64_t>(piece, N - n0);
-        float *buf = c->d_stage + (size_t)(k & 1) * piece * D;
-        if (k >= 2) cudaStreamWaitEvent(cs, used[k & 1], 0);
+        const int b = k % NSTAGE;
+        float *buf = c->d_stage + (size_t)b * piece * D;
+        if (k >= NSTAGE) cudaStreamWaitEvent(cs, c->h_used[b], 0);
         if (cudaMemcpyAsync(buf, Y_host + n0 * D, sizeof(float) * n * D, cudaMemcpyHostToDevice,
                             cs) != cudaSuccess) {
             set_error("H2D copy failed");
             rc = PROSPER_ECUDA;
             break;
         }
-        cudaEventRecord(copied[k & 1], cs);
-        cudaStreamWaitEvent(s, copied[k & 1], 0);
+        cudaEventRecord(c->h_copied[b], cs);
+        cudaStreamWaitEvent(s, c->h_copied[b], 0);
         rc = estep_piece(c, p, buf, n, &st, s);
-        cudaEventRecord(used[k & 1], s);
+        cudaEventRecord(c->h_used[b], s);
     }
     if (!rc) rc = estep_end(c, &st, s);
     if (!rc) {
@@ -429,9 +444,6 @@ int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_h
     cudaMemcpyAsync(&status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     cudaStreamSynchronize(cs);
-    for (int i = 0; i < 2; ++i) { cudaEventDestroy(copied[i]); cudaEventDestroy(used[i]); }
-    cudaEventDestroy(start);
-    cudaStreamDestroy(cs);
     if (rc) return rc;
     if (e != cudaSuccess) { set_error("stream failed: %s", cudaGetErrorString(e)); return PROSPER_ECUDA; }
     if (status & ST_NONFINITE) {

@@ -52,7 +52,7 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
 __global__ void __launch_bounds__(AT_NT, 1)
 k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const float *__restrict__ es,
            int64_t N, int D, int H, int Hp, int halves, uint32_t tmem_cols, float *__restrict__ part,
-           unsigned *__restrict__ status) {
+           int accumulate, unsigned *__restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t lbar[2], cbar[2];   // data of half q arrived / MMAs of half q done
     __shared__ uint32_t tmem_slot;
@@ -262,9 +262,10 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
         if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
         aborted = true;
     }
-    // ---- epilogue: this CTA's FP32 partial of A^T to global memory (plain
-    //      stores; k_reduce_parts sums the partials in FP64 in a fixed order)
-    if (!aborted && conv) {
+    // ---- epilogue: this CTA's FP32 partial of A^T to global memory (stored by
+    //      the first launch of an E-step, added to by the later ones; the
+    //      partials are summed once per E-step by k_reduce_parts)
+    if (!aborted && conv && (!accumulate || done_tiles > 0)) {
         const int qd = warp & 3;
         const int h_in = qd * 32 + lane;
         const int cb = (warp < 4) ? 0 : D / 2, ce = (warp < 4) ? D / 2 : D;
@@ -282,7 +283,14 @@ k_astat_tc(const float *__restrict__ Y, const int32_t *__restrict__ sel, const f
                 if (h < H) {
                     float4 *dst = reinterpret_cast<float4 *>(mine + (size_t)h * D + c0);
 #pragma unroll
-                    for (int k = 0; k < 16; k += 4) dst[k / 4] = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                    for (int k = 0; k < 16; k += 4) {
+                        float4 o = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                        if (accumulate) {
+                            const float4 a = dst[k / 4];
+                            o.x += a.x; o.y += a.y; o.z += a.z; o.w += a.w;
+                        }
+                        dst[k / 4] = o;
+                    }
                 }
             }
         }
@@ -341,7 +349,7 @@ __global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int64
 
 bool astat_tc_ok(int D, int H) { return D % 64 == 0 && D <= 256 && H <= 256 && (D / 2) % 16 == 0; }
 
-int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s) {
+int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s) {
     if (N <= 0) return PROSPER_OK;
     const int D = c->D, H = c->H;
     const int halves = (H + 127) / 128;
@@ -355,16 +363,25 @@ int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaS
     }
     uint32_t cols = 32;
     while ((int)cols < halves * D) cols <<= 1;
-    const int64_t ntiles = (N + AT_T - 1) / AT_T;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
-    TraceScope tr(c, "astat_tc", s, 2);
+    // one CTA per SM whatever N is, so that every partial is written by the
+    // first launch of the E-step (CTAs without tiles store zeros)
+    const int grid = c->num_sms;
+    TraceScope tr(c, "astat_tc", s);
     k_astat_tc<<<grid, AT_NT, smem, s>>>(Y, c->sel, c->es, N, D, H, c->Hp, halves, cols, c->apart,
-                                         c->d_status);
+                                         c->apart_pieces > 0 ? 1 : 0, c->d_status);
     PROSPER_LAUNCH_CHECK();
-    const int64_t HD = (int64_t)H * D;
+    ++c->apart_pieces;
+    return PROSPER_OK;
+}
+
+int finish_astat_tc(prosper_ctx *c, double *At, cudaStream_t s) {
+    if (c->apart_pieces == 0) return PROSPER_OK;
+    const int64_t HD = (int64_t)c->H * c->D;
+    TraceScope tr(c, "astat_tc_reduce", s);
     k_reduce_parts<<<(int)std::min<int64_t>((HD + 255) / 256, 4 * c->num_sms), 256, 0, s>>>(
-        c->apart, grid, HD, At);
+        c->apart, c->num_sms, HD, At);
     PROSPER_LAUNCH_CHECK();
+    c->apart_pieces = 0;
     return PROSPER_OK;
 }
 

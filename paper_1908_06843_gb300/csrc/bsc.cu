@@ -881,7 +881,7 @@ int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStre
     if (N <= 0) return PROSPER_OK;
     if (astat_tc_ok(c->D, c->H) && c->apart && !c->astat_simt &&
         (reinterpret_cast<uintptr_t>(Y) & 15) == 0)   // bulk copies need 16-byte aligned rows
-        return launch_astat_tc(c, Y, N, At, s);
+        return launch_astat_tc(c, Y, N, s);
     const int H = c->H, D = c->D;
     const size_t smem = sizeof(float) * ((size_t)H * AD + AT * AD + AT * PROSPER_MAX_HPRIME) +
                         sizeof(int) * (AT * PROSPER_MAX_HPRIME + 3 * (H + 1));

@@ -79,6 +79,7 @@ struct prosper_ctx {
     float *yy = nullptr;      // chunk x 2: y^T y as an unevaluated sum hi + lo
     float *es = nullptr;      // chunk x SEL_STRIDE posterior means <s> of the selected latents
     float *apart = nullptr;   // num_sms x H x D FP32 partials of sum y<s>^T (tensor-core path)
+    int apart_pieces = 0;     // tensor-core launches since the E-step began (partials pending)
 
     // M-step workspace (FP64)
     double *mB = nullptr;     // Hq x Hq (Hq = H rounded up to 32): B and its trailing updates
@@ -98,6 +99,8 @@ struct prosper_ctx {
     float *h_stage = nullptr;
     float *d_stage = nullptr;
     int64_t stage_points = 0;
+    cudaStream_t h_copy = nullptr;            // copy stream of prosper_estep_host
+    cudaEvent_t h_copied[3] = {}, h_used[3] = {}, h_start = nullptr;
 
     prosper::ServeState *serve = nullptr;
     prosper::TraceState *trace = nullptr;
@@ -118,7 +121,8 @@ int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_
                       prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
                       float *mapp_out, float *logz_out, cudaStream_t s);
 int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s);
-int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s);
+int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s);
+int finish_astat_tc(prosper_ctx *c, double *At, cudaStream_t s);
 bool astat_tc_ok(int D, int H);
 int launch_symmetrize(prosper_ctx *c, double *B, cudaStream_t s);
 
