@@ -387,12 +387,16 @@ int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_h
     // ~160 us, longer than its E-step work, so the copies run back to back
     // (smaller pieces leave the kernels too little work to fill the GPU)
     constexpr int NSTAGE = 3;
-    const int64_t piece = std::min<int64_t>(c->chunk, 32768);
+    const int64_t cap = std::min<int64_t>(c->chunk, 32768);
+    // equal pieces (multiples of 128 points): the work left after the last copy
+    // is then one piece's E-step, not a full piece plus a remainder
+    const int64_t npieces = N > 0 ? (N + cap - 1) / cap : 1;
+    const int64_t piece = std::min<int64_t>(cap, ((N + npieces - 1) / npieces + 127) / 128 * 128);
     const size_t H = c->H, D = c->D;
     if (!c->d_stage) {
-        size_t bytes = sizeof(float) * NSTAGE * (size_t)piece * D;
+        size_t bytes = sizeof(float) * NSTAGE * (size_t)cap * D;
         PROSPER_CUDA_TRY(cudaMalloc(&c->d_stage, bytes));
-        c->stage_points = piece;
+        c->stage_points = cap;
     }
     if (!c->h_copy) {
         PROSPER_CUDA_TRY(cudaStreamCreateWithFlags(&c->h_copy, cudaStreamNonBlocking));
@@ -420,7 +424,7 @@ int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_h
     for (int64_t n0 = 0; n0 < N && !rc; n0 += piece, ++k) {
         const int64_t n = std::min<int64_t>(piece, N - n0);
         const int b = k % NSTAGE;
-        float *buf = c->d_stage + (size_t)b * piece * D;
+        float *buf = c->d_stage + (size_t)b * cap * D;
         if (k >= NSTAGE) cudaStreamWaitEvent(cs, c->h_used[b], 0);
         if (cudaMemcpyAsync(buf, Y_host + n0 * D, sizeof(float) * n * D, cudaMemcpyHostToDevice,
                             cs) != cudaSuccess) {
