@@ -33,7 +33,7 @@ struct McaArgs {
     const float *Y;        // N x D
     const double *theta;
     int64_t N;
-    int D, H, Hp, gamma;
+    int D, H, Hp, gamma, nK;   // nK = number of states per point
     double *mca;           // 2 H D (estep) or NULL
     double *scal;
     int16_t *sel_out, *map_out;
@@ -62,7 +62,8 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // shared layout: W (H x D), log2 W (H x D), W transposed (D x H), 1/sum_d W_dh (H), per warp
-// { l[KMAX], mask[KMAX] } and, with SMEM_STATS, per warp sum<A>y and sum<A> (H x D each)
+// { l[KW], mask[KW], 32 x 33 partial sums } (KW = max(nK, D, 64) rounded to 4) and,
+// with SMEM_STATS, per warp sum<A>y and sum<A> (H x D each)
 // acc (hi, lo) += v with Knuth's TwoSum (hi + lo carries about 48 bits)
 __device__ __forceinline__ void two_sum_acc(float2 &acc, float v) {
     const float s = acc.x + v;
@@ -83,9 +84,12 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
     float *Rc = WsT + H * D;
     float *wl = Rc + ((H + 3) & ~3);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *ell = wl + warp * 2 * KMAX;
-    unsigned *msk = reinterpret_cast<unsigned *>(ell + KMAX);
-    float *Ay = wl + MW * 2 * KMAX + (size_t)warp * 2 * H * D;   // SMEM_STATS only
+    const int KW = (max(max(A.nK, D), 64) + 3) & ~3;
+    const int WSTR = 2 * KW + 32 * 33;
+    float *ell = wl + warp * WSTR;
+    unsigned *msk = reinterpret_cast<unsigned *>(ell + KW);
+    float *part = ell + 2 * KW;                                   // 32 x 33 partial sums
+    float *Ay = wl + MW * WSTR + (size_t)warp * 2 * H * D;        // SMEM_STATS only
     float *Aa = Ay + H * D;
 
     for (int i = tid; i < H * D; i += MW * 32) {
@@ -162,18 +166,34 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
             const unsigned ball = __ballot_sync(0xffffffffu, lane < Hp && rank == j);
             I[j] = ball ? __shfl_sync(0xffffffffu, myh, __ffs(ball) - 1) : 0;
         }
-        // ---- pass 1: depth-first over states, l in log2 units relative to s = 0
+        // ---- pass 1: depth-first over states, l in log2 units relative to s = 0.
+        //      Each lane's share of |y - f|^2 - |y|^2 goes to a 32 x 33 tile;
+        //      every 32 states, lane s adds up row s (conflict-free: the pitch of
+        //      33 words puts (s, l) in bank (s + l) mod 32), so no state waits on
+        //      its own cross-lane reduction.
         int nv = 0;
-        float m = -INFINITY;
+        float mloc = -INFINITY;
+        auto flush = [&](int v0, int cnt) {
+            __syncwarp();
+            if (lane < cnt) {
+                float r = 0.f;
+#pragma unroll 8
+                for (int l2 = 0; l2 < 32; ++l2) r += part[lane * 33 + l2];
+                const float l = lpi * (float)__popc(msk[v0 + lane]) - ih * r;
+                ell[v0 + lane] = l;
+                mloc = fmaxf(mloc, l);
+            }
+            __syncwarp();
+        };
         auto visit = [&](unsigned mask, const float (&f)[DK]) {
             float r = 0.f;
 #pragma unroll
             for (int k = 0; k < DK; ++k) r = fmaf(f[k], f[k] - 2.f * y[k], r);   // |y-f|^2 - |y|^2
-            r = warp_sum(r);
-            const float l = lpi * (float)__popc(mask) - ih * r;
-            if (lane == 0) { ell[nv] = l; msk[nv] = mask; }
-            m = fmaxf(m, l);
+            const int slot = nv & 31;
+            part[slot * 33 + lane] = r;
+            if (lane == 0) msk[nv] = mask;
             ++nv;
+            if (slot == 31) flush(nv - 32, 32);
         };
         if (gamma > 5) {
             // generic order (any gamma <= H'): every pattern with <= gamma units,
@@ -260,7 +280,8 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
                 }
             }
         }
-        __syncwarp();
+        if (nv & 31) flush(nv & ~31, nv & 31);
+        const float m = warp_max(mloc);
         // ---- normalisation, posterior means, MAP (lanes over states)
         float Z = 0.f, es[PROSPER_MAX_HPRIME];
 #pragma unroll
@@ -380,7 +401,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
     }
     if (SMEM_STATS) {
         __syncthreads();
-        float *base = wl + MW * 2 * KMAX;
+        float *base = wl + MW * WSTR;
         for (int i = tid; i < 2 * H * D; i += MW * 32) {
             float s = 0.f;
             for (int w = 0; w < MW; ++w) s += base[(size_t)w * 2 * H * D + i];
@@ -389,8 +410,9 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
     }
 }
 
-size_t mca_smem(int D, int H, bool smem_stats) {
-    size_t f = 3 * (size_t)H * D + ((H + 3) & ~3) + (size_t)MW * 2 * KMAX;
+size_t mca_smem(int D, int H, int nK, bool smem_stats) {
+    const size_t kw = (size_t)((std::max(std::max(nK, D), 64) + 3) & ~3);
+    size_t f = 3 * (size_t)H * D + ((H + 3) & ~3) + (size_t)MW * (2 * kw + 32 * 33);
     if (smem_stats) f += (size_t)MW * 2 * H * D;
     return f * sizeof(float);
 }
@@ -410,8 +432,8 @@ int mca_launch(McaArgs &A, int grid, size_t smem, cudaStream_t s) {
 
 template <int DK>
 int mca_dispatch(McaArgs &A, bool enc, int grid, cudaStream_t s) {
-    const bool ss = mca_smem(A.D, A.H, true) <= 227 * 1024;
-    const size_t smem = mca_smem(A.D, A.H, ss && !enc);
+    const bool ss = mca_smem(A.D, A.H, A.nK, true) <= 227 * 1024;
+    const size_t smem = mca_smem(A.D, A.H, A.nK, ss && !enc);
     if (enc) return mca_launch<DK, true, false>(A, grid, smem, s);
     if (ss) return mca_launch<DK, false, true>(A, grid, smem, s);
     return mca_launch<DK, false, false>(A, grid, smem, s);
@@ -427,7 +449,11 @@ int launch_mca_estep(prosper_ctx *c, const float *W, const double *theta, const 
     if (N <= 0) return PROSPER_OK;
     McaArgs A;
     A.W = W; A.Y = Y; A.theta = theta; A.N = N;
-    A.D = c->D; A.H = c->H; A.Hp = c->Hp; A.gamma = c->gamma;
+    A.D = c->D; A.H = c->H; A.Hp = c->Hp; A.gamma = c->gamma; A.nK = c->nK;
+    if (c->nK > KMAX) {
+        set_error("MCA: %d states per point > %d", c->nK, KMAX);
+        return PROSPER_EINVAL;
+    }
     A.mca = st ? st->mca : nullptr;
     A.scal = st ? st->scal : nullptr;
     A.sel_out = sel_out; A.map_out = map_out; A.smean_out = smean_out; A.mapp_out = mapp_out;
