@@ -341,3 +341,31 @@ def test_tensor_core_and_simt_astat_agree(orc):
         torch.cuda.synchronize()
         out.append(st["At"].cpu().numpy())
     assert relfro(out[0], out[1]) <= 1e-6, relfro(out[0], out[1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_estep_host_pieces_match_device(precision):
+    """prosper_estep_host (Y in pinned host memory, copied in equal pieces
+    through staging buffers, A-statistic partials carried across pieces)
+    gives the statistics of the one-launch device E-step on the same points:
+    the same candidates and posteriors, only the FP32 partial sums of
+    sum y<s>^T are added in another order."""
+    from paper_1908_06843_gb300 import Context
+    d = synth.gabor(N=70_001, seed=1002)          # three pieces, the last one ragged
+    Y = np.ascontiguousarray(d["Y"], np.float32)
+    Wt = np.asarray(d["Wt"], np.float32)
+    ctx = Context(0, 256, 256, 10, 5, precision)
+    W = torch.tensor(Wt, device="cuda")
+    theta = torch.tensor([4 / 256, 0.2, 0.0, 0.0], dtype=torch.float64, device="cuda")
+    P = ctx.params(W, theta)
+    st = ctx.alloc_stats()
+    ctx.estep(P, torch.tensor(Y, device="cuda"), st)
+    torch.cuda.synchronize()
+    dev = torch_stats_to_numpy(st)
+    Yh = torch.from_numpy(Y).pin_memory()
+    host = ctx.estep_host(P, Yh)
+    assert relfro(host["At"], dev["At"]) <= 1e-6, relfro(host["At"], dev["At"])
+    assert relfro(host["B"], dev["B"]) <= 1e-12, relfro(host["B"], dev["B"])
+    assert host["scal"][3] == dev["scal"][3] == len(Y)
+    for k in (0, 1, 2):
+        assert abs(host["scal"][k] - dev["scal"][k]) <= 1e-9 * abs(dev["scal"][k])
