@@ -67,44 +67,65 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled during the timed region.
+
+    nvidia-smi runs from before the warm-up (so that it is sampling when the
+    timed region starts); every line is time-stamped on arrival and only the
+    lines that arrive between mark_start() and mark_stop() (plus one sampling
+    interval) are reported."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 10
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "50", "-i", str(self.gpu)],
+                 "-lms", str(self.PERIOD_MS), "-i", str(self.gpu)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.perf_counter() + 3.0
+            while not self.lines and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_stop(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
                     "samples": 0}
+        time.sleep(2 * self.PERIOD_MS / 1000.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
+        lo = self.t0 if self.t0 is not None else -1e30
+        hi = (self.t1 if self.t1 is not None else 1e30) + self.PERIOD_MS / 1000.0
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if not (lo <= ts <= hi):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -118,7 +139,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "period_ms": self.PERIOD_MS}
 
 
 def dist_info():
@@ -193,22 +215,26 @@ def run_reference(args):
 
 
 def bench_form(torch, ctx, P, Yg, st, steps, warmup, dist, sampler):
+    if sampler:
+        sampler.start()
     for _ in range(warmup):
         ctx.estep(P, Yg, st)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    if sampler:
-        sampler.start()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.mark_start()
     e0.record(stream)
     for _ in range(steps):
         ctx.estep(P, Yg, st)
     e1.record(stream)
     torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_stop()
     clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
     if dist is not None:
