@@ -51,9 +51,11 @@ extern "C" {
 #define PROSPER_GSC 2  /* Gaussian sparse coding: s_h = b_h z_h, b ~ Bernoulli(pi), z_h ~ N(mu_h, psi_h) */
 
 /* Precision of the BSC preselection projection W^T y (other models: FP32 only). */
-#define PROSPER_FP32          0  /* FP32 SIMT projection */
-#define PROSPER_BF16_RESCORE  1  /* BF16 tensor-core (tcgen05) projection for the selection only;
-                                    the H' selected projections are recomputed in FP32 */
+#define PROSPER_FP32          0  /* FP32 SIMT projection; exact top-H' of the FP32 scores */
+#define PROSPER_BF16_RESCORE  1  /* BF16 tensor-core (tcgen05) projection of the unit-norm rows
+                                    W_h/||W_h|| for the selection only, ranked on the score
+                                    rounded to 15 mantissa bits (ties to the lower h); the H'
+                                    selected projections are recomputed in FP32 */
 
 /* Limits.  BSC/MCA: 1 <= Hprime <= 10; GSC: Hprime <= 10 and gamma <= 3;
  * 0 <= gamma <= Hprime <= H; BSC/MCA/GSC H <= 256; D <= 1024.
@@ -120,7 +122,7 @@ int prosper_estep(prosper_ctx *ctx, const prosper_params *p, const float *Y, int
                   prosper_stats *out, void *stream);
 
 /* Closed-form M-step ("Model.step", Sec. 3) from statistics of N points:
- * BSC/GSC W = A B^{-1} (FP64 Cholesky), pi = sum<|s|>/(N H),
+ * BSC/GSC W = A B^{-1} (FP64, blocked Cholesky of B), pi = sum<|s|>/(N H),
  * sigma^2 = (sum y^T y - 2 tr(W^T A) + tr(W^T W B))/(N D) with the new W;
  * GSC also mu_h, psi_h; MCA the rho-smoothed-max update of W (clamped >= 1e-6),
  * pi as BSC, sigma^2 = sum<||y - f||^2>/(N D).  A unit with B_hh <= 1e-9 N
@@ -161,10 +163,13 @@ int prosper_encode_noalloc(int D, int H, int Hprime, int gamma, const float *W,
                            void *stream);
 
 /* Same E-step as prosper_estep with Y and the statistics in HOST memory:
- * Y_host (N x D) is copied to the device in pieces, the statistics are copied
- * back into host arrays At_host (H x D), B_host (H x H), scal_host
- * (PROSPER_SC_LEN) (each may be NULL), and the call returns after the stream
- * has finished.  p (W, theta, mu, psi) stays on the device. */
+ * Y_host (N x D) is copied to the device in equal pieces of at most 32,768
+ * points, overlapped with the kernels of the previous pieces (page-locked
+ * Y_host lets the copies run asynchronously; pageable memory works but the
+ * copies then stall the host), the statistics are copied back into host
+ * arrays At_host (H x D), B_host (H x H), scal_host (PROSPER_SC_LEN) (each may
+ * be NULL), and the call returns after the stream has finished.  p (W, theta,
+ * mu, psi) stays on the device. */
 int prosper_estep_host(prosper_ctx *ctx, const prosper_params *p, const float *Y_host,
                        int64_t N, double *At_host, double *B_host, double *scal_host,
                        void *stream);
