@@ -157,7 +157,9 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
     float *Ws = sm;                                  // D x H (transposed: lane h reads row d)
     float *Gs = Ws + H * D;                          // H x H
     unsigned *Ks = reinterpret_cast<unsigned *>(Gs + H * H);   // nK canonical masks
-    float *wbase = reinterpret_cast<float *>(Ks + ((nK + 3) & ~3));
+    float *mus = reinterpret_cast<float *>(Ks + ((nK + 3) & ~3));   // mu (H)
+    float *mpr = mus + ((H + 3) & ~3);                                // mu / psi (H)
+    float *wbase = mpr + ((H + 3) & ~3);
     float *acc = wbase + warp * (S::N * 32 + 64 + 3 * H + H * D);   // per warp
     unsigned *scratch = reinterpret_cast<unsigned *>(acc + S::N * 32);
     float *gpart = acc + S::N * 32 + 64;             // 3H
@@ -165,6 +167,16 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 
     for (int i = tid; i < H * D; i += GW * 32) Ws[(i % D) * H + i / D] = A.W[i];
     float *ysm = wbase + (size_t)GW * (S::N * 32 + 64 + 3 * H + H * D) + (size_t)warp * D;   // per warp
+    // per warp: the subset-table row of each state, read from global memory in
+    // the log-joint pass and reused by the moment pass (same lane, same state)
+    float *trow = reinterpret_cast<float *>(
+                      (reinterpret_cast<uintptr_t>(wbase + (size_t)GW * (S::N * 32 + 64 + 3 * H + H * D + D)) + 15) &
+                      ~static_cast<uintptr_t>(15)) +
+                  (size_t)warp * nK * TAB;   // 16-byte aligned (float4 stores)
+    for (int h = tid; h < H; h += GW * 32) {
+        mus[h] = A.mu[h];
+        mpr[h] = A.mu[h] / A.psi[h];
+    }
     for (int i = tid; i < H * H; i += GW * 32) Gs[i] = A.G[i];
     if (tid == 0) {   // canonical state masks: by size, then lexicographic
         int n = 0;
@@ -276,7 +288,11 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
                         if (i < k) rk += binom3(bg[i], i + 1);
-                    const float *t = A.tab + rk * TAB;
+                    const float4 *t4 = reinterpret_cast<const float4 *>(A.tab + rk * TAB);
+                    const float4 ta = __ldg(t4), tb = __ldg(t4 + 1);
+                    reinterpret_cast<float4 *>(trow + v * TAB)[0] = ta;
+                    reinterpret_cast<float4 *>(trow + v * TAB)[1] = tb;
+                    const float t[7] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z};
                     float mi[3][3];
                     mi[0][0] = t[1]; mi[0][1] = mi[1][0] = t[2]; mi[0][2] = mi[2][0] = t[3];
                     mi[1][1] = t[4]; mi[1][2] = mi[2][1] = t[5]; mi[2][2] = t[6];
@@ -287,7 +303,7 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 #pragma unroll
                         for (int j = 0; j < HP; ++j) pv = (j == bl[i]) ? pI[j] : pv;
                         p[i] = (i < k) ? pv : 0.f;
-                        mu[i] = (i < k) ? A.mu[bg[i]] : 0.f;
+                        mu[i] = (i < k) ? mus[bg[i]] : 0.f;
                     }
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
@@ -333,11 +349,7 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 #pragma unroll
             for (int j = 0; j < HP; ++j)
                 if (((mk >> j) & 1u) && q < 3) { bl[q] = j; bg[q] = I[j]; ++q; }
-            int rk = (k > 1 ? H : 0) + (k > 2 ? H * (H - 1) / 2 : 0);   // first index of the size-k block
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-                if (i < k) rk += binom3(bg[i], i + 1);
-            const float *t = A.tab + rk * TAB;
+            const float *t = trow + v * TAB;     // stored by this lane in the log-joint pass
             float mi[3][3];
             mi[0][0] = t[1]; mi[0][1] = mi[1][0] = t[2]; mi[0][2] = mi[2][0] = t[3];
             mi[1][1] = t[4]; mi[1][2] = mi[2][1] = t[5]; mi[2][2] = t[6];
@@ -347,7 +359,7 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
                 float pv = 0.f;
 #pragma unroll
                 for (int j = 0; j < HP; ++j) pv = (j == bl[i]) ? pI[j] : pv;
-                w[i] = (i < k) ? pv * is2 + A.mu[bg[i]] / A.psi[bg[i]] : 0.f;
+                w[i] = (i < k) ? pv * is2 + mpr[bg[i]] : 0.f;
             }
             float kap[3];
 #pragma unroll
@@ -460,9 +472,10 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
 template <int HP>
 size_t gsc_smem(int D, int H, int nK) {
     using S = Slots<HP>;
-    size_t f = (size_t)H * D + (size_t)H * H + ((nK + 3) & ~3);
+    size_t f = (size_t)H * D + (size_t)H * H + ((nK + 3) & ~3) + 2 * (size_t)((H + 3) & ~3);
     f += (size_t)GW * (S::N * 32 + 64 + 3 * H + H * D);
-    f += (size_t)GW * D;   // per-warp y buffers
+    f += (size_t)GW * D;                 // per-warp y buffers
+    f += (size_t)GW * nK * TAB + 4;      // per-warp subset-table rows (+ alignment slack)
     return f * sizeof(float);
 }
 
