@@ -7,7 +7,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -20,6 +22,20 @@ void set_error(const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+int ensure_smem_attr(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> done;
+    int dev = 0;
+    PROSPER_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = done[std::make_pair(dev, func)];
+    if (bytes > cur) {
+        PROSPER_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        cur = bytes;
+    }
+    return PROSPER_OK;
 }
 
 struct TraceRec {
@@ -47,7 +63,7 @@ TraceScope::~TraceScope() {
     if (on) cudaEventRecord(c->trace->recs[idx].b, s);
 }
 
-static int num_states(int Hp, int gamma) {
+int num_states(int Hp, int gamma) {
     double c = 0.0, b = 1.0;
     for (int k = 0; k <= gamma && k <= Hp; ++k) {
         c += b;
@@ -161,6 +177,11 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     if (model == PROSPER_GSC && H > 32) { set_error("GSC: H=%d > 32", H); return PROSPER_EINVAL; }
     if ((model == PROSPER_GSC || model == PROSPER_MCA) && D > 256) {
         set_error("MCA/GSC: D=%d > 256", D);
+        return PROSPER_EINVAL;
+    }
+    if (model == PROSPER_GSC && gsc_smem_bytes(D, H, Hprime, num_states(Hprime, gamma)) > 227 * 1024) {
+        set_error("GSC: D=%d, H=%d, Hprime=%d, gamma=%d need %zu bytes of shared memory per CTA (> 227 KB)",
+                  D, H, Hprime, gamma, gsc_smem_bytes(D, H, Hprime, num_states(Hprime, gamma)));
         return PROSPER_EINVAL;
     }
     if (precision != PROSPER_FP32 && precision != PROSPER_BF16_RESCORE) {

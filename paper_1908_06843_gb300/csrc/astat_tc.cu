@@ -355,12 +355,7 @@ int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s) {
     const int halves = (H + 127) / 128;
     const size_t smem = 1024 + (size_t)2 * halves * 128 * 128 + (size_t)2 * D * 128 +
                         (size_t)AT_T * D * 4;
-    static size_t attr = 0;
-    if (smem > attr) {
-        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_astat_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-        attr = smem;
-    }
+    if (int rc = ensure_smem_attr((const void *)k_astat_tc, smem)) return rc;
     uint32_t cols = 32;
     while ((int)cols < halves * D) cols <<= 1;
     // one CTA per SM whatever N is, so that every partial is written by the

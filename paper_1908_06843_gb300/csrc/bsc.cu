@@ -823,13 +823,8 @@ int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
 
 int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s) {
     if (N <= 0) return PROSPER_OK;
-    static bool attr_done = false;
     const size_t smem = sizeof(ProjSmem);
-    if (!attr_done) {
-        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_bsc_proj_f32,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done = true;
-    }
+    if (int rc = ensure_smem_attr((const void *)k_bsc_proj_f32, smem)) return rc;
     int64_t ntiles = (N + PT - 1) / PT;
     int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_f32", s);
@@ -885,12 +880,7 @@ int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStre
     const int H = c->H, D = c->D;
     const size_t smem = sizeof(float) * ((size_t)H * AD + AT * AD + AT * PROSPER_MAX_HPRIME) +
                         sizeof(int) * (AT * PROSPER_MAX_HPRIME + 3 * (H + 1));
-    static size_t attr_smem = 0;
-    if (smem > attr_smem) {
-        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_astat, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
-        attr_smem = smem;
-    }
+    if (int rc = ensure_smem_attr((const void *)k_astat, smem)) return rc;
     const int slices = (D + AD - 1) / AD;
     int ranges = std::max(1, 2 * c->num_sms / slices);
     int64_t per = (N + ranges - 1) / ranges;

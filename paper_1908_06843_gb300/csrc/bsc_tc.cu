@@ -388,12 +388,7 @@ int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t
         return PROSPER_EINVAL;
     }
     const size_t smem = bf16_smem_bytes(c->D, c->H);
-    static size_t attr = 0;
-    if (smem > attr) {
-        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_bsc_proj_bf16,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = smem;
-    }
+    if (int rc = ensure_smem_attr((const void *)k_bsc_proj_bf16, smem)) return rc;
     uint32_t cols = 32;
     while ((int)cols < c->H) cols <<= 1;
     const int64_t ntiles = (N + TM - 1) / TM;

@@ -469,14 +469,19 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
     }
 }
 
-template <int HP>
-size_t gsc_smem(int D, int H, int nK) {
-    using S = Slots<HP>;
+size_t gsc_smem_hp(int D, int H, int Hp, int nK) {
+    const size_t slots = 2 * (size_t)Hp + (size_t)Hp * (Hp + 1) / 2;   // Slots<Hp>::N
     size_t f = (size_t)H * D + (size_t)H * H + ((nK + 3) & ~3) + 2 * (size_t)((H + 3) & ~3);
-    f += (size_t)GW * (S::N * 32 + 64 + 3 * H + H * D);
+    f += (size_t)GW * (slots * 32 + 64 + 3 * H + H * D);
     f += (size_t)GW * D;                 // per-warp y buffers
     f += (size_t)GW * nK * TAB + 4;      // per-warp subset-table rows (+ alignment slack)
     return f * sizeof(float);
+}
+
+template <int HP>
+size_t gsc_smem(int D, int H, int nK) {
+    static_assert(Slots<HP>::N == 2 * HP + HP * (HP + 1) / 2, "slot count");
+    return gsc_smem_hp(D, H, HP, nK);
 }
 
 template <int HP, int DK>
@@ -486,16 +491,9 @@ int gsc_launch2(GscArgs &A, bool enc, int grid, cudaStream_t s) {
         set_error("GSC: shared memory %zu bytes exceeds the limit (reduce D or H)", smem);
         return PROSPER_EINVAL;
     }
-    static size_t attr[2] = {0, 0};
-    if (smem > attr[enc]) {
-        if (enc)
-            PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_gsc_estep<HP, DK, true>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        else
-            PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_gsc_estep<HP, DK, false>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr[enc] = smem;
-    }
+    if (int rc = ensure_smem_attr(enc ? (const void *)k_gsc_estep<HP, DK, true>
+                                      : (const void *)k_gsc_estep<HP, DK, false>, smem))
+        return rc;
     if (enc) k_gsc_estep<HP, DK, true><<<grid, GW * 32, smem, s>>>(A);
     else k_gsc_estep<HP, DK, false><<<grid, GW * 32, smem, s>>>(A);
     PROSPER_LAUNCH_CHECK();
@@ -514,6 +512,8 @@ int gsc_launch(GscArgs &A, bool enc, int grid, cudaStream_t s) {
 }
 
 }  // namespace
+
+size_t gsc_smem_bytes(int D, int H, int Hp, int nK) { return gsc_smem_hp(D, H, Hp, nK); }
 
 int launch_gsc_prep(prosper_ctx *c, const prosper_params *p, cudaStream_t s) {
     int rc = launch_bsc_prep(c, p->W, s);     // G = W^T W (and 1/||W_h||)

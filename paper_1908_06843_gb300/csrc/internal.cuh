@@ -14,6 +14,17 @@ namespace prosper {
 // ---------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);
 
+// Raise `func`'s dynamic shared-memory limit on the CURRENT device to at least
+// `bytes`.  cudaFuncSetAttribute applies to one device only, so the value set
+// is remembered per (device, kernel) under a lock; every launcher that needs
+// more than 48 KB calls this before each launch (a map lookup when nothing
+// changes).  Returns PROSPER_OK or PROSPER_ECUDA (with set_error).
+int ensure_smem_attr(const void *func, size_t bytes);
+
+// |K| = sum_{k <= gamma} C(Hp, k): binary states with at most gamma active units
+// among Hp candidates.
+int num_states(int Hp, int gamma);
+
 #define PROSPER_CUDA_TRY(expr)                                                     \
     do {                                                                           \
         cudaError_t _e = (expr);                                                   \
@@ -132,6 +143,7 @@ int launch_mca_estep(prosper_ctx *c, const float *W, const double *theta, const 
                      int16_t *map_out, float *mapp_out, float *logz_out, cudaStream_t s);
 
 int launch_gsc_prep(prosper_ctx *c, const prosper_params *p, cudaStream_t s);
+size_t gsc_smem_bytes(int D, int H, int Hp, int nK);   // shared memory of the GSC E-step kernel
 int launch_gsc_estep(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
                      prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
                      float *mapp_out, float *logz_out, cudaStream_t s);

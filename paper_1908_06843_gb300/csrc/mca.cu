@@ -419,12 +419,7 @@ size_t mca_smem(int D, int H, int nK, bool smem_stats) {
 
 template <int DK, bool ENC, bool SS>
 int mca_launch(McaArgs &A, int grid, size_t smem, cudaStream_t s) {
-    static size_t attr = 0;
-    if (smem > attr) {
-        PROSPER_CUDA_TRY(cudaFuncSetAttribute(k_mca_estep<DK, ENC, SS>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = smem;
-    }
+    if (int rc = ensure_smem_attr((const void *)k_mca_estep<DK, ENC, SS>, smem)) return rc;
     k_mca_estep<DK, ENC, SS><<<grid, MW * 32, smem, s>>>(A);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;

@@ -20,6 +20,10 @@
 // streams, or from two host threads) race on the array and give undefined
 // results: issue them on one stream or serialise them.
 //
+// Non-finite input is not reported on this path (there is no context whose
+// status word a caller could read): a point whose y holds NaN or Inf gets a
+// non-finite log Z, which the caller can test.
+//
 // The first call on each device looks up the device address of the array
 // (cudaGetSymbolAddress, with that device current); make that first call
 // before any stream capture begins.
@@ -50,9 +54,10 @@ int g_num_sms[kMaxDevices] = {};
 
 // Per-device set-up: the device address of the scratch array (host code only
 // sees a host-side stand-in under its name).
-int scratch_for_current_device(float **out, int *num_sms) {
+int scratch_for_current_device(float **out, int *num_sms, int *device) {
     int dev = 0;
     PROSPER_CUDA_TRY(cudaGetDevice(&dev));
+    *device = dev;
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("device ordinal %d beyond %d", dev, kMaxDevices);
         return PROSPER_EINVAL;
@@ -107,14 +112,18 @@ extern "C" int prosper_encode_noalloc(int D, int H, int Hprime, int gamma, const
     if (N == 0) return PROSPER_OK;
     float *base = nullptr;
     int sms = 0;
-    int rc = scratch_for_current_device(&base, &sms);
+    int dev = 0;
+    int rc = scratch_for_current_device(&base, &sms, &dev);
     if (rc) return rc;
 
-    // a context on the host stack whose scratch pointers all point into the array
-    prosper_ctx c;
+    // a context on the host stack whose scratch pointers all point into the
+    // array; value-initialised, so every member not set here is zero / null
+    prosper_ctx c{};
     c.model = PROSPER_BSC; c.D = D; c.H = H; c.Hp = Hprime; c.gamma = gamma;
     c.precision = PROSPER_FP32;
+    c.nK = num_states(Hprime, gamma);
     c.chunk = NA_N;
+    c.device = dev;
     c.num_sms = sms;
     c.G = base + OFF_G;
     c.rnorm = base + OFF_RN;

@@ -352,6 +352,44 @@ def test_mca_mstep_large_rho_is_hard_argmax(orc):
     np.testing.assert_allclose(W2[m], np.maximum(num[m] / den[m], 1e-6), rtol=2e-3)
 
 
+def read_mca_selection_golden():
+    """The hand-worked MCA preselection case of tests/golden/mca_selection.txt."""
+    W, y, score, sel = [], None, None, {}
+    with open(os.path.join(GOLDEN, "mca_selection.txt")) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "W":
+                W.append([float(v) for v in t[1:]])
+            elif t[0] == "y":
+                y = np.array([float(v) for v in t[1:]])
+            elif t[0] == "score":
+                score = np.array([float(v) for v in t[1:]])
+            elif t[0] == "sel":
+                sel[int(t[1])] = [int(v) for v in t[2:]]
+    return np.array(W), y, score, sel
+
+
+def test_mca_selection_known_answer(orc):
+    """MCA preselection (Table 1 MCA row; score S_h = sum_d W_dh y_d / sum_d W_dh,
+    ties to the lower h) against scores and candidate sets worked by hand, with
+    three exactly tied scores.  A wrong normaliser (L2 norm, none) or the
+    reversed tie rule selects a different set at Hprime = 2."""
+    Wt, y, score, sel = read_mca_selection_golden()
+    H = Wt.shape[0]
+    got = orc.scores(orc.MCA, y, Wt)
+    np.testing.assert_array_equal(got, score)      # exact: every value is a dyadic fraction
+    for Hp, want in sel.items():
+        post = orc.posterior(orc.MCA, y, Wt, 0.2, 1.0, Hp, 1, rho=20)
+        assert post["sel"].tolist() == want, (Hp, post["sel"], want)
+    # the sets the wrong readings would give differ from the golden one
+    l2 = (Wt @ y) / np.linalg.norm(Wt, axis=1)
+    assert sorted(np.lexsort((np.arange(H), -l2))[:2].tolist()) != sel[2]
+    raw = Wt @ y
+    assert sorted(np.lexsort((np.arange(H), -raw))[:2].tolist()) != sel[2]
+
+
 # ---------------------------------------------------------------------------
 # GSC
 # ---------------------------------------------------------------------------

@@ -60,6 +60,35 @@ def test_noalloc_matches_encode_twice():
         assert float((got["logZ"] - ref["logZ"]).abs().max()) <= 1e-5 * float(ref["logZ"].abs().max()), call
 
 
+@pytest.mark.parametrize("D,H,Hp,gamma,N", [(25, 10, 6, 3, 1000),   # bars shape: D % 4 != 0
+                                             (30, 17, 5, 0, 300),     # gamma = 0: only s = 0
+                                             (30, 17, 1, 1, 65)])     # Hprime = 1
+def test_noalloc_small_shapes_match_encode(D, H, Hp, gamma, N):
+    """Shapes below the array's maximum (the fixed offsets and the D- and
+    H-dependent strides), D not a multiple of 4 (scalar Y loads), gamma = 0 and
+    Hprime = 1, twice in a row, against prosper_encode."""
+    from paper_1908_06843_gb300 import Context, binding
+    lib = binding.load()
+    dev = torch.device("cuda")
+    ctx = Context(0, D, H, Hp, gamma, 0)
+    g = synth.rng(D + H + Hp)
+    for call in range(2):
+        Wt = g.standard_normal((H, D)).astype(np.float32)
+        Y = (g.standard_normal((N, D)) * 1.5).astype(np.float32)
+        W = torch.tensor(Wt, device=dev)
+        theta = torch.tensor([0.15, 1.0, 0.0, 0.0], dtype=torch.float64, device=dev)
+        Yg = torch.tensor(Y, device=dev)
+        got = _encode_noalloc(lib, D, H, Hp, gamma, W, theta, Yg)
+        ref = ctx.encode(ctx.params(W, theta), Yg)
+        torch.cuda.synchronize()
+        assert torch.equal(got["sel"], ref["sel"]), call
+        if gamma > 0:
+            assert torch.equal(got["map_idx"], ref["map_idx"]), call
+        assert float((got["s_mean"] - ref["s_mean"]).abs().max()) <= 1e-5, call
+        assert float((got["map_p"] - ref["map_p"]).abs().max()) <= 1e-5, call
+        assert float((got["logZ"] - ref["logZ"]).abs().max()) <= 1e-5 * float(ref["logZ"].abs().max()), call
+
+
 def test_noalloc_rejects_sizes_beyond_its_array():
     from paper_1908_06843_gb300 import binding
     lib = binding.load()
