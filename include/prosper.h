@@ -68,6 +68,12 @@ extern "C" {
 #define PROSPER_TH_PI    0   /* prior activation probability pi                   */
 #define PROSPER_TH_SIGMA 1   /* observation noise standard deviation sigma         */
 #define PROSPER_TH_RHO   2   /* MCA: exponent rho of the smoothed max in the M-step */
+#define PROSPER_TH_T     3   /* posterior temperature T of deterministic annealing
+                                (Sec. 3, LinearAnnealing): every E-step uses
+                                q_n(s) ~ p(s, y_n)^(1/T) on K_n and reports
+                                log Z_n = T log sum_{s in K_n} p(s, y_n)^(1/T);
+                                a value <= 0 is read as T = 1 (no annealing).
+                                The M-step does not read or change it. */
 #define PROSPER_THETA_LEN 4
 
 /* scal[] layout of the scalar sufficient statistics (device doubles). */

@@ -30,8 +30,10 @@ _OUT = os.path.join(_HERE, "_build", "libprosper_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BSC, MCA, GSC = 0, 1, 2
-SC_F, SC_S1, SC_YY, SC_N, SC_MCA_R2, SC_LEN = 0, 1, 2, 3, 4, 8
+BSC, MCA, GSC, TSC, DSC = 0, 1, 2, 3, 4
+SC_F, SC_S1, SC_YY, SC_N, SC_MCA_R2, SC_DSC0, SC_LEN = 0, 1, 2, 3, 4, 5, 8
+TH_LEN = 12
+TSC_VALUES = (-1.0, 1.0)
 
 
 def build(force: bool = False) -> str:
@@ -54,8 +56,10 @@ def _load():
             i32, i64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_double
             _lib.orc_num_states.argtypes = [i32, i32]
             _lib.orc_states.argtypes = [i32, i32, P, i32]
-            _lib.orc_estep.argtypes = [i32, i64, i32, i32, i32, i32] + [P] * 16 + [i32]
-            _lib.orc_posterior.argtypes = [i32, i32, i32, i32, i32] + [P] * 13
+            _lib.orc_num_states_m.argtypes = [i32, i32, i32]
+            _lib.orc_states_dsc.argtypes = [i32, i32, i32, P, P, i32]
+            _lib.orc_estep.argtypes = [i32, i64, i32, i32, i32, i32] + [P] * 17 + [i32]
+            _lib.orc_posterior.argtypes = [i32, i32, i32, i32, i32] + [P] * 14
             _lib.orc_scores.argtypes = [i32, i32, i32] + [P] * 6
             _lib.orc_mstep.argtypes = [i32, i32, i32, dbl] + [P] * 9
     return _lib
@@ -81,27 +85,64 @@ def states(Hp: int, gamma: int) -> np.ndarray:
     return out
 
 
-def theta_vec(pi, sigma, rho=0.0):
-    return np.array([pi, sigma, rho], dtype=np.float64)
+def theta_vec(pi, sigma, rho=0.0, T=1.0, vals=None, pvals=None):
+    """The oracle's theta: {pi, sigma, rho, T, p_1..p_3, m, phi_1..phi_3, 0}.
+    T is the posterior temperature of deterministic annealing (q ~ p(s, y)^(1/T);
+    1 = the plain truncated posterior).  DSC: vals = the m <= 3 nonzero values
+    phi_v, pvals = their prior probabilities."""
+    th = np.zeros(TH_LEN)
+    th[:4] = [pi, sigma, rho, T]
+    if vals is not None:
+        m = len(vals)
+        assert 1 <= m <= 3 and len(pvals) == m
+        th[4:4 + m] = pvals
+        th[7] = m
+        th[8:8 + m] = vals
+    return th
+
+
+def num_states_m(Hp: int, gamma: int, m: int) -> int:
+    """sum_{k <= gamma} C(Hp, k) m^k: discrete states with m nonzero values."""
+    return _load().orc_num_states_m(Hp, gamma, m)
+
+
+def states_dsc(Hp: int, gamma: int, m: int):
+    """Canonical discrete states: (unit masks, value codes: 2 bits per nonzero unit)."""
+    n = num_states_m(Hp, gamma, m)
+    masks = np.zeros(n, dtype=np.uint32)
+    codes = np.zeros(n, dtype=np.uint32)
+    _load().orc_states_dsc(Hp, gamma, m, _p(masks), _p(codes), n)
+    return masks, codes
+
+
+def _values(model, vals):
+    if model == TSC:
+        return np.array(TSC_VALUES)
+    if model == DSC:
+        return np.asarray(vals, np.float64)
+    return np.array([1.0])
 
 
 def estep(model, Y, Wt, pi, sigma, Hp, gamma, rho=0.0, mu=None, psi=None,
-          sel_in=None, nthreads=0):
-    """Truncated E-step over all rows of Y.  Returns a dict of numpy arrays:
-    sel, smean, map_idx, map_p, logZ (per point) and At, B, scal, gsc, mca."""
+          sel_in=None, nthreads=0, T=1.0, vals=None, pvals=None):
+    """Truncated E-step over all rows of Y (at posterior temperature T).
+    Returns a dict of numpy arrays: sel, smean, map_idx, map_val, map_p, logZ
+    (per point; logZ = T log sum_{K_n} p(s, y_n)^(1/T)) and At, B, scal, gsc,
+    mca.  DSC: vals / pvals are the nonzero values and their probabilities."""
     lib = _load()
     Y = _f64(Y)
     Wt = _f64(Wt)
     N, D = Y.shape
     H = Wt.shape[0]
-    th = theta_vec(pi, sigma, rho)
+    th = theta_vec(pi, sigma, rho, T, vals, pvals)
     mu, psi = _f64(mu), _f64(psi)
     if model == GSC:
         assert mu is not None and psi is not None
     si = None if sel_in is None else np.ascontiguousarray(sel_in, dtype=np.int32)
     out = dict(
         sel=np.zeros((N, Hp), np.int32), smean=np.zeros((N, Hp)),
-        map_idx=np.zeros((N, max(gamma, 1)), np.int32), map_p=np.zeros(N),
+        map_idx=np.zeros((N, max(gamma, 1)), np.int32), map_val=np.zeros((N, max(gamma, 1))),
+        map_p=np.zeros(N),
         logZ=np.zeros(N), At=np.zeros((H, D)), B=np.zeros((H, H)),
         scal=np.zeros(SC_LEN),
         gsc=np.zeros(3 * H) if model == GSC else None,
@@ -109,49 +150,55 @@ def estep(model, Y, Wt, pi, sigma, Hp, gamma, rho=0.0, mu=None, psi=None,
     )
     rc = lib.orc_estep(model, N, D, H, Hp, gamma, _p(Y), _p(Wt), _p(th), _p(mu), _p(psi),
                        _p(si), _p(out["sel"]), _p(out["smean"]),
-                       _p(out["map_idx"]) if gamma > 0 else None, _p(out["map_p"]),
+                       _p(out["map_idx"]) if gamma > 0 else None,
+                       _p(out["map_val"]) if gamma > 0 else None, _p(out["map_p"]),
                        _p(out["logZ"]), _p(out["At"]), _p(out["B"]), _p(out["scal"]),
                        _p(out["gsc"]), _p(out["mca"]), int(nthreads))
     if rc != 0:
         raise ValueError(f"orc_estep failed ({rc})")
     if gamma == 0:
         out["map_idx"] = np.zeros((N, 0), np.int32)
+        out["map_val"] = np.zeros((N, 0))
     if out["mca"] is not None:
         out["mca"] = out["mca"].reshape(2, H, D)
     return out
 
 
-def posterior(model, y, Wt, pi, sigma, Hp, gamma, rho=0.0, mu=None, psi=None, sel_in=None):
-    """Full truncated posterior of one point: dict(sel, masks, ell, q, kappa, lambda, scores)."""
+def posterior(model, y, Wt, pi, sigma, Hp, gamma, rho=0.0, mu=None, psi=None, sel_in=None,
+              T=1.0, vals=None, pvals=None):
+    """Full truncated posterior of one point at temperature T:
+    dict(sel, masks, vcodes, ell (log p(s, y)), q, kappa, lambda, scores)."""
     lib = _load()
     y = _f64(y)
     Wt = _f64(Wt)
     H, D = Wt.shape
-    nK = num_states(Hp, gamma)
-    th = theta_vec(pi, sigma, rho)
+    nK = num_states_m(Hp, gamma, len(_values(model, vals)))
+    th = theta_vec(pi, sigma, rho, T, vals, pvals)
     mu, psi = _f64(mu), _f64(psi)
     si = None if sel_in is None else np.ascontiguousarray(sel_in, dtype=np.int32)
     sel = np.zeros(Hp, np.int32)
     masks = np.zeros(nK, np.uint32)
+    vcodes = np.zeros(nK, np.uint32)
     ell = np.zeros(nK)
     q = np.zeros(nK)
     kappa = np.zeros((nK, Hp)) if model == GSC else None
     lam = np.zeros((nK, Hp, Hp)) if model == GSC else None
     scores = np.zeros(H)
     rc = lib.orc_posterior(model, D, H, Hp, gamma, _p(y), _p(Wt), _p(th), _p(mu), _p(psi),
-                           _p(si), _p(sel), _p(masks), _p(ell), _p(q), _p(kappa), _p(lam),
-                           _p(scores))
+                           _p(si), _p(sel), _p(masks), _p(vcodes), _p(ell), _p(q), _p(kappa),
+                           _p(lam), _p(scores))
     if rc < 0:
         raise ValueError("orc_posterior failed")
-    return dict(sel=sel, masks=masks, ell=ell, q=q, kappa=kappa, lam=lam, scores=scores)
+    return dict(sel=sel, masks=masks, vcodes=vcodes, ell=ell, q=q, kappa=kappa, lam=lam,
+                scores=scores)
 
 
-def scores(model, y, Wt, pi=0.5, sigma=1.0, mu=None, psi=None):
+def scores(model, y, Wt, pi=0.5, sigma=1.0, mu=None, psi=None, vals=None, pvals=None):
     lib = _load()
     y = _f64(y)
     Wt = _f64(Wt)
     H, D = Wt.shape
-    th = theta_vec(pi, sigma)
+    th = theta_vec(pi, sigma, vals=vals, pvals=pvals)
     out = np.zeros(H)
     lib.orc_scores(model, D, H, _p(y), _p(Wt), _p(th), _p(_f64(mu)), _p(_f64(psi)), _p(out))
     return out
@@ -172,6 +219,22 @@ def mstep(model, N, stats, Wt, pi, sigma, mu=None, psi=None):
     if rc != 0:
         raise ValueError(f"orc_mstep failed ({rc})")
     return Wt, th[0], th[1], mu, psi
+
+
+def mstep_dsc(model, N, stats, Wt, pi, sigma, vals=None, pvals=None):
+    """Closed-form M-step of TSC / DSC.  Returns (Wt_new, pi_new, sigma_new,
+    pvals_new): TSC pi = the fraction of nonzero units (p(+-1) = pi/2); DSC
+    the new probability of each nonzero value (pi_new = their sum)."""
+    lib = _load()
+    Wt = np.array(Wt, dtype=np.float64, copy=True)
+    H, D = Wt.shape
+    th = theta_vec(pi, sigma, vals=vals, pvals=pvals)
+    rc = lib.orc_mstep(model, D, H, float(N), _p(_f64(stats["At"])), _p(_f64(stats["B"])),
+                       _p(_f64(stats["scal"])), None, None, _p(Wt), _p(th), None, None)
+    if rc != 0:
+        raise ValueError(f"orc_mstep failed ({rc})")
+    m = len(vals) if vals is not None else 0
+    return Wt, th[0], th[1], th[4:4 + m].copy()
 
 
 def exact_em_free_energy(model, Y, Wt, pi, sigma, rho=0.0, mu=None, psi=None):

@@ -10,7 +10,10 @@
  * What it computes (paper: Exarchakis et al., "ProSper", JMLR MLOSS):
  *   - The generative model template of Eq. 1-2: a prior p(s|Theta) and a
  *     noise model p(y|s,Theta) = p(y; f(Theta,s)), with the per-model prior,
- *     noise and superposition f from Table 1 (rows BSC, GSC, MCA).
+ *     noise and superposition f from Table 1 (rows BSC, TSC, DSC, GSC, MCA).
+ *     TSC and DSC are linear superpositions like BSC with latents taking
+ *     values in a finite set Phi = {0, phi_1, .., phi_m} under a categorical
+ *     prior (TSC: Phi = {-1, 0, 1}, zero-mean: p(-1) = p(1) = pi/2).
  *   - EM with truncated posteriors (Sec. 2): for each data point n a set of
  *     H' candidate latents I_n is preselected, the state set K_n holds every
  *     binary pattern over I_n with at most gamma active units (the
@@ -39,10 +42,18 @@
 #include <omp.h>
 #endif
 
-enum { ORC_BSC = 0, ORC_MCA = 1, ORC_GSC = 2 };
+enum { ORC_BSC = 0, ORC_MCA = 1, ORC_GSC = 2, ORC_TSC = 3, ORC_DSC = 4 };
 
-/* scal[] layout of the aggregated scalar statistics */
-enum { SC_F = 0, SC_S1 = 1, SC_YY = 2, SC_N = 3, SC_MCA_R2 = 4, SC_LEN = 8 };
+/* scal[] layout of the aggregated scalar statistics; SC_DSC0 + v holds
+ * sum_n sum_h <[s_h = phi_{v+1}]> (TSC/DSC: expected count of each nonzero value) */
+enum { SC_F = 0, SC_S1 = 1, SC_YY = 2, SC_N = 3, SC_MCA_R2 = 4, SC_DSC0 = 5, SC_LEN = 8 };
+
+/* theta[] of the oracle: pi, sigma, rho, T, then for DSC the prior
+ * probabilities of the m nonzero values (4 .. 4+m-1), m (7) and the values
+ * phi_1 .. phi_m (8 .. 8+m-1). */
+enum { TH_PI = 0, TH_SIGMA = 1, TH_RHO = 2, TH_T = 3, TH_DSC_P = 4, TH_DSC_M = 7, TH_DSC_V = 8,
+       TH_LEN = 12 };
+#define MAXV 3   /* nonzero values of a discrete latent */
 
 static const double LOG_2PI = 1.8378770664093454835606594728112;
 
@@ -76,6 +87,45 @@ int orc_states(int Hp, int gamma, uint32_t *masks, int cap) {
             if (n < cap) masks[n] = m;
             ++n;
             /* next combination in lexicographic order */
+            int i = k - 1;
+            while (i >= 0 && idx[i] == Hp - k + i) --i;
+            if (i < 0) break;
+            ++idx[i];
+            for (int j = i + 1; j < k; ++j) idx[j] = idx[j - 1] + 1;
+        }
+    }
+    return n;
+}
+
+/* Discrete latents (TSC, DSC): every pattern of at most gamma nonzero units,
+ * each nonzero unit taking one of m values.  Canonical order: by number of
+ * nonzero units, then the lexicographic order of their sorted local indices,
+ * then the lexicographic order of their value indices (0 .. m-1, in unit
+ * order).  vcodes[n] holds the value index of the a-th nonzero unit in bits
+ * 2a, 2a+1.  With m = 1 this is the binary order of orc_states. */
+int orc_num_states_m(int Hp, int gamma, int m) {
+    double c = 0.0, mk = 1.0;
+    for (int k = 0; k <= gamma && k <= Hp; ++k) { c += binom(Hp, k) * mk; mk *= m; }
+    return (int)(c + 0.5);
+}
+
+int orc_states_dsc(int Hp, int gamma, int m, uint32_t *masks, uint32_t *vcodes, int cap) {
+    int n = 0;
+    int idx[32];
+    for (int k = 0; k <= gamma && k <= Hp; ++k) {
+        for (int i = 0; i < k; ++i) idx[i] = i;
+        for (;;) {
+            uint32_t mk = 0;
+            for (int i = 0; i < k; ++i) mk |= 1u << idx[i];
+            uint32_t nv = 1;
+            for (int i = 0; i < k; ++i) nv *= (uint32_t)m;
+            for (uint32_t c = 0; c < nv; ++c) {
+                /* c in base m, most significant digit = first unit */
+                uint32_t code = 0, r = c;
+                for (int a = k - 1; a >= 0; --a) { code |= (r % (uint32_t)m) << (2 * a); r /= (uint32_t)m; }
+                if (n < cap) { masks[n] = mk; if (vcodes) vcodes[n] = code; }
+                ++n;
+            }
             int i = k - 1;
             while (i >= 0 && idx[i] == Hp - k + i) --i;
             if (i < 0) break;
@@ -143,8 +193,13 @@ typedef struct {
     int model, D, H, Hp, gamma, nK;
     const double *Wt;      /* H x D */
     double pi, sigma, rho; /* sigma = noise standard deviation */
+    double T;              /* posterior temperature of deterministic annealing (1 = none) */
     const double *mu, *psi;/* GSC: slab means and variances (H each) */
     const uint32_t *K;     /* nK canonical state masks over local units */
+    const uint32_t *V;     /* nK value codes (2 bits per nonzero unit, in unit order) */
+    int m;                 /* number of nonzero values (1 for the binary models) */
+    double phi[MAXV];      /* the nonzero values (binary models: phi_1 = 1) */
+    double lp0, lpv[MAXV]; /* log prior probability of 0 and of each nonzero value */
 } problem_t;
 
 /* Per-thread scratch for one data point. */
@@ -178,6 +233,17 @@ static void scratch_free(scratch_t *s) {
 static double log_prior(const problem_t *p, int k) {
     return k * log(p->pi) + (p->H - k) * log(1.0 - p->pi);
 }
+
+/* Categorical prior of a discrete state (Table 1, TSC and DSC): every unit
+ * independently 0 with probability pi_0, phi_v with probability pi_v. */
+static double log_prior_dsc(const problem_t *p, uint32_t mask, uint32_t vcode) {
+    int k = popcount32(mask);
+    double l = (p->H - k) * p->lp0;
+    for (int a = 0; a < k; ++a) l += p->lpv[(vcode >> (2 * a)) & 3u];
+    return l;
+}
+
+static int is_discrete(const problem_t *p) { return p->model == ORC_TSC || p->model == ORC_DSC; }
 
 /* Gaussian log-density N(y; m, v I_D) with v = sigma^2, from ||y - m||^2. */
 static double log_gauss_iso(int D, double sigma, double r2) {
@@ -260,10 +326,19 @@ static void selection_scores(const problem_t *p, scratch_t *s, const double *y) 
     int D = p->D;
     for (int h = 0; h < p->H; ++h) {
         const double *w = p->Wt + (size_t)h * D;
-        if (p->model == ORC_BSC) {
+        if (p->model == ORC_BSC || is_discrete(p)) {
+            /* BSC: W_h^T y / ||W_h||.  TSC/DSC (reading): the largest normalised
+             * projection a nonzero value can reach, sign(phi) W_h^T y / ||W_h||
+             * maximised over phi in Phi \ {0}: |.| when Phi has both signs. */
             double pr = 0.0, nn = 0.0;
             for (int d = 0; d < D; ++d) { pr += w[d] * y[d]; nn += w[d] * w[d]; }
-            s->score[h] = nn > 0.0 ? pr / sqrt(nn) : 0.0;
+            double sc = nn > 0.0 ? pr / sqrt(nn) : 0.0;
+            if (is_discrete(p)) {
+                int pos = 0, neg = 0;
+                for (int v = 0; v < p->m; ++v) { pos |= p->phi[v] > 0.0; neg |= p->phi[v] < 0.0; }
+                sc = (pos && neg) ? fabs(sc) : (neg ? -sc : sc);
+            }
+            s->score[h] = sc;
         } else if (p->model == ORC_MCA) {
             double pr = 0.0, sw = 0.0;
             for (int d = 0; d < D; ++d) { pr += w[d] * y[d]; sw += w[d]; }
@@ -297,13 +372,25 @@ static void select_top(const problem_t *p, const double *score, int *sel) {
  * Log-joint log p(s, y | Theta) of state K[kk] over selection sel.
  * ---------------------------------------------------------------------- */
 static double log_joint(const problem_t *p, scratch_t *s, const double *y,
-                        const int *sel, uint32_t mask, double *kappa, double *lambda) {
+                        const int *sel, uint32_t mask, uint32_t vcode, double *kappa,
+                        double *lambda) {
     int D = p->D, k = popcount32(mask);
     int gidx[32], a = 0;
     for (int j = 0; j < p->Hp; ++j)
         if (mask & (1u << j)) gidx[a++] = sel[j];
     if (p->model == ORC_GSC)
         return log_prior(p, k) + gsc_marginal(p, s, y, gidx, k, kappa, lambda, p->Hp);
+    if (is_discrete(p)) {
+        /* f(Theta, s) = W s with s_{gidx[i]} = phi of its value index */
+        double r2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            double f = 0.0;
+            for (int i = 0; i < k; ++i)
+                f += p->phi[(vcode >> (2 * i)) & 3u] * p->Wt[(size_t)gidx[i] * D + d];
+            r2 += (y[d] - f) * (y[d] - f);
+        }
+        return log_prior_dsc(p, mask, vcode) + log_gauss_iso(D, p->sigma, r2);
+    }
     /* f(Theta, s): BSC linear superposition W s; MCA max_h W_dh s_h (0 if s=0) */
     for (int d = 0; d < D; ++d) {
         double f = 0.0;
@@ -328,6 +415,7 @@ typedef struct {
     double ss[32 * 32];        /* <s_{I_i} s_{I_j}> */
     double bmean[32];          /* GSC: <b_{I_j}> */
     double sabs;               /* <|s|> (number of active units) */
+    double vcnt[MAXV];         /* TSC/DSC: <number of units with value phi_v> */
     double r2;                 /* MCA: <||y - f(s)||^2> */
 } point_t;
 
@@ -347,16 +435,22 @@ static void point_estep(const problem_t *p, scratch_t *s, const double *y,
     for (int kk = 0; kk < nK; ++kk) {
         double *kap = s->kappa + (size_t)kk * Hp, *lam = s->lambda + (size_t)kk * Hp * Hp;
         /* GSC: kappa/lambda are compacted over the active units of the state */
-        double l = log_joint(p, s, y, o->sel, p->K[kk],
+        double l = log_joint(p, s, y, o->sel, p->K[kk], p->V[kk],
                              p->model == ORC_GSC ? kap : NULL,
                              p->model == ORC_GSC ? lam : NULL);
         s->ell[kk] = l;
         if (l > m) { m = l; arg = kk; }      /* first maximum in canonical order */
     }
+    /* Deterministic annealing (Sec. 3, LinearAnnealing; reading): the posterior
+     * at temperature T is q_T(s) = p(s,y)^(1/T) / sum_{s' in K_n} p(s',y)^(1/T),
+     * and the per-point free energy is T log sum_{s in K_n} p(s,y)^(1/T)
+     * (= log sum_{K_n} p(s,y) at T = 1).  With m = max_s log p(s,y):
+     *   T log sum exp(l/T) = m + T log sum exp((l - m)/T). */
+    const double T = p->T;
     double Z = 0.0;
-    for (int kk = 0; kk < nK; ++kk) Z += exp(s->ell[kk] - m);
-    o->logZ = m + log(Z);
-    for (int kk = 0; kk < nK; ++kk) s->q[kk] = exp(s->ell[kk] - o->logZ);
+    for (int kk = 0; kk < nK; ++kk) Z += exp((s->ell[kk] - m) / T);
+    o->logZ = m + T * log(Z);
+    for (int kk = 0; kk < nK; ++kk) s->q[kk] = exp((s->ell[kk] - m) / T) / Z;
     o->map_state = arg;
     o->map_p = s->q[arg];
     memset(o->smean, 0, sizeof(o->smean));
@@ -364,10 +458,28 @@ static void point_estep(const problem_t *p, scratch_t *s, const double *y,
     memset(o->bmean, 0, sizeof(o->bmean));
     o->sabs = 0.0;
     o->r2 = 0.0;
+    memset(o->vcnt, 0, sizeof(o->vcnt));
     for (int kk = 0; kk < nK; ++kk) {
         uint32_t mask = p->K[kk];
         double q = s->q[kk];
         o->sabs += q * popcount32(mask);
+        if (is_discrete(p)) {
+            /* <s_i> = sum_s q(s) s_i and <s_i s_j> with the units' values */
+            int loc[32], k = 0;
+            double val[32];
+            for (int j = 0; j < Hp; ++j)
+                if (mask & (1u << j)) {
+                    int v = (int)((p->V[kk] >> (2 * k)) & 3u);
+                    o->vcnt[v] += q;
+                    val[k] = p->phi[v];
+                    loc[k++] = j;
+                }
+            for (int a = 0; a < k; ++a) {
+                o->smean[loc[a]] += q * val[a];
+                for (int c = 0; c < k; ++c) o->ss[loc[a] * 32 + loc[c]] += q * val[a] * val[c];
+            }
+            continue;
+        }
         if (p->model == ORC_GSC) {
             const double *kap = s->kappa + (size_t)kk * Hp, *lam = s->lambda + (size_t)kk * Hp * Hp;
             int loc[32], k = 0;
@@ -429,36 +541,54 @@ static void problem_init(problem_t *p, int model, int D, int H, int Hp, int gamm
                          const double *Wt, const double *theta, const double *mu,
                          const double *psi, uint32_t **Kbuf) {
     p->model = model; p->D = D; p->H = H; p->Hp = Hp; p->gamma = gamma;
-    p->Wt = Wt; p->pi = theta[0]; p->sigma = theta[1]; p->rho = theta[2];
+    p->Wt = Wt; p->pi = theta[TH_PI]; p->sigma = theta[TH_SIGMA]; p->rho = theta[TH_RHO];
+    p->T = theta[TH_T] > 0.0 ? theta[TH_T] : 1.0;   /* theta[3] <= 0 selects T = 1 */
     p->mu = mu; p->psi = psi;
-    p->nK = orc_num_states(Hp, gamma);
-    *Kbuf = malloc(sizeof(uint32_t) * p->nK);
-    orc_states(Hp, gamma, *Kbuf, p->nK);
+    /* value set and categorical prior: binary models phi = {1}, prior pi;
+     * TSC phi = {-1, 1} with pi/2 each; DSC from theta */
+    p->m = 1; p->phi[0] = 1.0;
+    double pv[MAXV] = {p->pi, 0.0, 0.0};
+    if (model == ORC_TSC) {
+        p->m = 2; p->phi[0] = -1.0; p->phi[1] = 1.0;
+        pv[0] = pv[1] = 0.5 * p->pi;
+    } else if (model == ORC_DSC) {
+        p->m = (int)theta[TH_DSC_M];
+        for (int v = 0; v < p->m; ++v) { p->phi[v] = theta[TH_DSC_V + v]; pv[v] = theta[TH_DSC_P + v]; }
+    }
+    double p0 = 1.0;
+    for (int v = 0; v < p->m; ++v) { p0 -= pv[v]; p->lpv[v] = log(pv[v]); }
+    p->lp0 = log(p0);
+    p->nK = orc_num_states_m(Hp, gamma, p->m);
+    *Kbuf = malloc(sizeof(uint32_t) * 2 * (size_t)p->nK);
+    orc_states_dsc(Hp, gamma, p->m, *Kbuf, *Kbuf + p->nK, p->nK);
     p->K = *Kbuf;
+    p->V = *Kbuf + p->nK;
 }
 
 /* ------------------------------------------------------------------------
  * orc_estep: full truncated E-step over N points.
  *
- * Inputs:  Y (N x D), Wt (H x D), theta = {pi, sigma, rho}, mu/psi (GSC, H
+ * Inputs:  Y (N x D), Wt (H x D), theta = {pi, sigma, rho, T}, mu/psi (GSC, H
  *          each; NULL otherwise), sel_in (N x Hp ascending global indices to
  *          use instead of preselection; NULL = preselect).
  * Per-point outputs (each may be NULL): sel (N x Hp), smean (N x Hp),
- *          map_idx (N x gamma, ascending, -1 padded), map_p (N), logZ (N).
+ *          map_idx (N x gamma, ascending, -1 padded), map_val (N x gamma: the
+ *          MAP state's value of each listed unit, 0 padded), map_p (N), logZ (N).
  * Aggregates (each may be NULL; overwritten):
  *          At (H x D): sum_n <s>_n y_n^T (A = sum y <s>^T, transposed)
  *          B  (H x H): sum_n <s s^T>_n
  *          scal[SC_LEN]: F = sum_n log sum_{K_n} p(s,y_n), sum <|s|>,
- *                        sum y^T y, N, MCA sum <||y - f||^2>
+ *                        sum y^T y, N, MCA sum <||y - f||^2>,
+ *                        TSC/DSC sum <count of value phi_v> (SC_DSC0 + v)
  *          gsc (3H): sum <b_h>, sum <s_h>, sum <s_h^2>
  *          mca (2 H D): sum <A_dh> y_d, sum <A_dh> (both H x D)
  * ---------------------------------------------------------------------- */
 int orc_estep(int model, int64_t N, int D, int H, int Hp, int gamma,
               const double *Y, const double *Wt, const double *theta,
               const double *mu, const double *psi, const int32_t *sel_in,
-              int32_t *sel, double *smean, int32_t *map_idx, double *map_p,
-              double *logZ, double *At, double *B, double *scal, double *gsc,
-              double *mca, int nthreads) {
+              int32_t *sel, double *smean, int32_t *map_idx, double *map_val,
+              double *map_p, double *logZ, double *At, double *B, double *scal,
+              double *gsc, double *mca, int nthreads) {
     if (Hp < 1 || Hp > 32 || Hp > H || gamma < 0 || gamma > Hp) return -1;
     problem_t p;
     uint32_t *Kbuf;
@@ -496,11 +626,19 @@ int orc_estep(int model, int64_t N, int D, int H, int Hp, int gamma,
             point_estep(&p, &s, y, sel_in ? (const int *)(sel_in + (size_t)n * Hp) : NULL, &o);
             if (sel) for (int j = 0; j < Hp; ++j) sel[(size_t)n * Hp + j] = o.sel[j];
             if (smean) for (int j = 0; j < Hp; ++j) smean[(size_t)n * Hp + j] = o.smean[j];
-            if (map_idx) {
-                uint32_t mk = p.K[o.map_state];
+            if (map_idx || map_val) {
+                uint32_t mk = p.K[o.map_state], vc = p.V[o.map_state];
                 int a = 0;
-                for (int j = 0; j < Hp; ++j) if (mk & (1u << j)) map_idx[(size_t)n * gamma + a++] = o.sel[j];
-                for (; a < gamma; ++a) map_idx[(size_t)n * gamma + a] = -1;
+                for (int j = 0; j < Hp; ++j)
+                    if (mk & (1u << j)) {
+                        if (map_idx) map_idx[(size_t)n * gamma + a] = o.sel[j];
+                        if (map_val) map_val[(size_t)n * gamma + a] = p.phi[(vc >> (2 * a)) & 3u];
+                        ++a;
+                    }
+                for (; a < gamma; ++a) {
+                    if (map_idx) map_idx[(size_t)n * gamma + a] = -1;
+                    if (map_val) map_val[(size_t)n * gamma + a] = 0.0;
+                }
             }
             if (map_p) map_p[n] = o.map_p;
             if (logZ) logZ[n] = o.logZ;
@@ -508,6 +646,7 @@ int orc_estep(int model, int64_t N, int D, int H, int Hp, int gamma,
             for (int d = 0; d < D; ++d) yy += y[d] * y[d];
             lS[SC_F] += o.logZ; lS[SC_S1] += o.sabs; lS[SC_YY] += yy; lS[SC_N] += 1.0;
             lS[SC_MCA_R2] += o.r2;
+            if (is_discrete(&p)) for (int v = 0; v < p.m; ++v) lS[SC_DSC0 + v] += o.vcnt[v];
             if (lAt) for (int j = 0; j < Hp; ++j) {
                 double e = o.smean[j];
                 double *row = lAt + (size_t)o.sel[j] * D;
@@ -545,15 +684,16 @@ int orc_estep(int model, int64_t N, int D, int H, int Hp, int gamma,
 
 /* ------------------------------------------------------------------------
  * orc_posterior: the full truncated posterior of ONE data point, for tests.
- * Outputs: sel (Hp), masks (nK), ell (nK log-joints), q (nK),
+ * Outputs: sel (Hp), masks (nK), vcodes (nK, TSC/DSC value codes; may be
+ * NULL), ell (nK log-joints), q (nK),
  * kappa (nK x Hp) and lambda (nK x Hp x Hp) for GSC (compacted over the
  * active units of each state; may be NULL).  Returns nK.
  * ---------------------------------------------------------------------- */
 int orc_posterior(int model, int D, int H, int Hp, int gamma, const double *y,
                   const double *Wt, const double *theta, const double *mu,
                   const double *psi, const int32_t *sel_in, int32_t *sel,
-                  uint32_t *masks, double *ell, double *q, double *kappa,
-                  double *lambda, double *scores) {
+                  uint32_t *masks, uint32_t *vcodes, double *ell, double *q,
+                  double *kappa, double *lambda, double *scores) {
     if (Hp < 1 || Hp > 32 || Hp > H || gamma < 0 || gamma > Hp) return -1;
     problem_t p;
     uint32_t *Kbuf;
@@ -567,6 +707,7 @@ int orc_posterior(int model, int D, int H, int Hp, int gamma, const double *y,
     for (int j = 0; j < Hp; ++j) sel[j] = o.sel[j];
     for (int kk = 0; kk < p.nK; ++kk) {
         masks[kk] = p.K[kk];
+        if (vcodes) vcodes[kk] = p.V[kk];
         ell[kk] = s.ell[kk];
         q[kk] = s.q[kk];
     }
@@ -598,7 +739,7 @@ int orc_scores(int model, int D, int H, const double *y, const double *Wt,
  * orc_mstep: closed-form M-step (Sec. 3, Model.step; the prior and noise
  * parameters are learned as well as W, Sec. 1).
  *
- * BSC, GSC (maximise the expected log-joint Q; exact argmax):
+ * BSC, TSC, DSC, GSC (maximise the expected log-joint Q; exact argmax):
  *   W = A B^{-1}  ->  Wt = B^{-1} At   (FP64 Cholesky)
  *   pi = sum<|s|> / (N H)
  *   sigma^2 = (sum y^T y - 2 tr(W^T A) + tr(W^T W B)) / (N D)   (new W)
@@ -664,8 +805,13 @@ int orc_mstep(int model, int D, int H, double Ntot, const double *At,
             t2 += g * B[(size_t)i * H + j];
         }
     double s2 = (scal[SC_YY] - 2.0 * t1 + t2) / (Ntot * D);
-    theta[0] = scal[SC_S1] / (Ntot * H);
-    theta[1] = sqrt(s2 > 0.0 ? s2 : 0.0);
+    /* Bernoulli (BSC, GSC spike) and zero-mean ternary (TSC: p(+-1) = pi/2):
+     * pi = expected fraction of nonzero units.  DSC: each nonzero value's
+     * probability = its expected fraction (the categorical argmax of Q). */
+    theta[TH_PI] = scal[SC_S1] / (Ntot * H);
+    theta[TH_SIGMA] = sqrt(s2 > 0.0 ? s2 : 0.0);
+    if (model == ORC_DSC)
+        for (int v = 0; v < (int)theta[TH_DSC_M]; ++v) theta[TH_DSC_P + v] = scal[SC_DSC0 + v] / (Ntot * H);
     if (model == ORC_GSC) {
         for (int h = 0; h < H; ++h) {
             double sb = gsc[h], ss = gsc[H + h], ss2 = gsc[2 * H + h];

@@ -402,7 +402,7 @@ struct StateArgs {
 // warp-uniform loop; units LB..HP-1 ("hi", HB = min(HP,5) of them) are
 // unrolled, so each lo pattern evaluates its 2^HB hi patterns from registers:
 //   l(lo, t) = L(lo) + sum_{u in t} c_u(lo) + M(t),   M(t) = sum_{u<v in t} b_uv,
-// with a_j = log2e (log(pi/(1-pi)) + (p_j - G_jj/2)/sigma^2), b_ij = -log2e G_ij/sigma^2.
+// with a_j = log2e (log(pi/(1-pi)) + (p_j - G_jj/2)/sigma^2) / T, b_ij = -log2e G_ij/(sigma^2 T).
 // Hi patterns are grouped by their number of active units; a group is skipped
 // by one warp-uniform branch when lo plus the group exceeds gamma units.
 // Pass 1 finds the maximum m; pass 2 forms e = 2^(l - m), the moments and the
@@ -424,15 +424,20 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     // log p(y, s=0) = c0 - y^T y / (2 sigma^2)
     // (the FP64 chains run in lane 0 of four different warps, i.e. on four
     // SM sub-partitions, while every thread loads its candidate list and G block)
+    // Deterministic annealing: every log-joint is divided by the temperature T
+    // (theta[3]; <= 0 reads as 1) before the log-sum-exp, so q ~ p(s,y)^(1/T) and
+    // log Z = T log sum_{K_n} p(s,y)^(1/T).
     __shared__ float s_lpi, s_is2;
-    __shared__ double s_c0, s_inv2s2;
+    __shared__ double s_c0, s_inv2s2, s_T;
     if ((threadIdx.x & 31) == 0) {
         const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
+        const double th = A.theta[PROSPER_TH_T];
+        const double T = th > 0.0 ? th : 1.0;
         const double s2 = sigma * sigma;
         switch (threadIdx.x >> 5) {
-            case 0: s_lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634); break;
-            case 1: s_is2 = (float)(1.4426950408889634 / s2); break;
-            case 2: s_c0 = A.H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2)); break;
+            case 0: s_lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634 / T); break;
+            case 1: s_is2 = (float)(1.4426950408889634 / (s2 * T)); break;
+            case 2: s_c0 = A.H * log(1.0 - pi) - 0.5 * A.D * (kLog2Pi + log(s2)); s_T = T; break;
             default: s_inv2s2 = 0.5 / s2; break;
         }
     }
@@ -599,7 +604,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     const float2 yyv = A.yy[nn];
     const double yy = (double)yyv.x + (double)yyv.y;
     const double logp0 = fma(-yy, s_inv2s2, s_c0);
-    const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp0;
+    const double logZ = ((double)m + (double)log2f(Z)) * (kLn2 * s_T) + logp0;
     // MAP state mask from the winning key
     const unsigned rmask = 0xFFFFu - (unsigned)(best & 0xFFFF);
     unsigned mapmask = 0u;

@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
     __syncthreads();
 
     const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
-    const float L2E = 1.4426950408889634f;
+    // deterministic annealing: log-joints divided by T (theta[3]; <= 0 reads as 1)
+    const double Tth = A.theta[PROSPER_TH_T];
+    const double T = Tth > 0.0 ? Tth : 1.0;
+    const float L2E = (float)(1.4426950408889634 / T);
     const float lpi = (float)log(pi / (1.0 - pi));
     const float is2 = (float)(1.0 / (sigma * sigma));
     const float is4 = is2 * is2;
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(GW * 32, 1) k_gsc_estep(GscArgs A) {
             acc[o * 32] = s * invZ;         // slot o, column 0 now holds the normalised value
         }
         __syncwarp();
-        const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp00 - (double)yy * i2s2;
+        const double logZ = ((double)m + (double)log2f(Z)) * (kLn2 * T) + logp00 - (double)yy * i2s2;
         if (ENCODE) {
             if (lane == 0) {
                 if (A.sel_out)

@@ -109,8 +109,11 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 
     const double pi = A.theta[PROSPER_TH_PI], sigma = A.theta[PROSPER_TH_SIGMA];
     const float rho = (float)A.theta[PROSPER_TH_RHO];
-    const float lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634);
-    const float ih = (float)(1.4426950408889634 / (2.0 * sigma * sigma));   // log2e / (2 sigma^2)
+    // deterministic annealing: log-joints divided by T (theta[3]; <= 0 reads as 1)
+    const double Tth = A.theta[PROSPER_TH_T];
+    const double T = Tth > 0.0 ? Tth : 1.0;
+    const float lpi = (float)(log(pi / (1.0 - pi)) * 1.4426950408889634 / T);
+    const float ih = (float)(1.4426950408889634 / (2.0 * sigma * sigma * T));   // log2e / (2 sigma^2 T)
     const double logp00 = H * log(1.0 - pi) - 0.5 * D * (kLog2Pi + log(sigma * sigma));
     const double i2s2 = 0.5 / (sigma * sigma);
 
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
         for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) es[j] = warp_sum(es[j]);
         best = __reduce_min_sync(0xffffffffu, (unsigned)best);
         const float invZ = 1.f / Z;
-        const double logZ = ((double)m + (double)log2f(Z)) * kLn2 + logp00 - (double)yy * i2s2;
+        const double logZ = ((double)m + (double)log2f(Z)) * (kLn2 * T) + logp00 - (double)yy * i2s2;
 
         if (ENCODE) {
             if (lane == 0) {

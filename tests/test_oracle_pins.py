@@ -147,6 +147,62 @@ def test_bsc_single_latent_logistic(orc):
         assert abs(post["q"][0] - (1 - expect)) < 1e-13
 
 
+# ---------------------------------------------------------------------------
+# Deterministic annealing (Sec. 3, LinearAnnealing): q_T(s) ~ p(s, y)^(1/T)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("T", [0.4, 2.5])
+@pytest.mark.parametrize("model", ["BSC", "MCA", "GSC"])
+def test_tempered_posterior_equals_bruteforce(orc, model, T):
+    """At temperature T and H' = H = gamma the oracle's posterior is the
+    softmax of log p(s, y)/T over all 2^H states and its per-point free energy
+    is T logsumexp(log p(s, y)/T), with log p(s, y) from scipy's densities."""
+    if model == "GSC":
+        Y, Wt, mu, psi = _small_gsc(3)
+        kw = dict(mu=mu, psi=psi)
+        brute = lambda y: brute_logjoint_gsc(y, Wt, 0.3, 0.6, mu, psi)
+    elif model == "MCA":
+        Y, Wt = _small_mca(3)
+        kw = dict(rho=20)
+        brute = lambda y: brute_logjoint_mca(y, Wt, 0.3, 0.6)
+    else:
+        Y, Wt = _small_bsc(3)
+        kw = {}
+        brute = lambda y: brute_logjoint_bsc(y, Wt, 0.3, 0.6)
+    m = getattr(orc, model)
+    H = Wt.shape[0]
+    for y in Y:
+        post = orc.posterior(m, y, Wt, 0.3, 0.6, H, H, T=T, **kw)
+        S, lj = brute(y)
+        idx = match_states(state_vectors(post, H), S)
+        np.testing.assert_allclose(post["q"], np.exp(lj / T - logsumexp(lj / T))[idx],
+                                   rtol=1e-10, atol=1e-14)
+    out = orc.estep(m, Y, Wt, 0.3, 0.6, H, H, T=T, **kw)
+    for n, y in enumerate(Y):
+        S, lj = brute(y)
+        assert abs(out["logZ"][n] - T * logsumexp(lj / T)) < 1e-9 * max(1.0, abs(out["logZ"][n]))
+
+
+def test_tempered_free_energy_is_the_variational_optimum(orc):
+    """For the truncated set K_n, T log sum_K p(s,y)^(1/T) = sum_K q_T log p(s,y)
+    + T H[q_T] (the maximum over q on K_n of E_q log p + T H[q], attained at
+    q_T); checked with ET (H' < H) at several T, including T = 1."""
+    Y, Wt = _small_bsc(4, H=8, D=9, N=4)
+    for T in (0.3, 1.0, 4.0):
+        out = orc.estep(orc.BSC, Y, Wt, 0.2, 0.7, 5, 3, T=T)
+        for n, y in enumerate(Y):
+            post = orc.posterior(orc.BSC, y, Wt, 0.2, 0.7, 5, 3, T=T)
+            q = post["q"]
+            ent = -np.sum(q[q > 0] * np.log(q[q > 0]))
+            assert abs(out["logZ"][n] - (q @ post["ell"] + T * ent)) < 1e-10 * max(1, abs(out["logZ"][n]))
+
+
+def test_high_temperature_gives_uniform_posterior(orc):
+    """T -> infinity: q_T -> uniform over the truncated set K_n."""
+    Y, Wt = _small_bsc(5, H=8, D=9, N=2)
+    post = orc.posterior(orc.BSC, Y[0], Wt, 0.2, 0.7, 6, 3, T=1e9)
+    np.testing.assert_allclose(post["q"], 1.0 / len(post["q"]), rtol=1e-6)
+
+
 def test_bsc_aggregates_are_scatter_of_point_moments(orc):
     """At = sum_n <s>_n y_n^T and diag(B) = sum_n <s_h>_n (binary s: s_h^2 = s_h),
     B symmetric, sum<|s|> = sum of <s>, F = sum log Z."""
@@ -388,6 +444,199 @@ def test_mca_selection_known_answer(orc):
     assert sorted(np.lexsort((np.arange(H), -l2))[:2].tolist()) != sel[2]
     raw = Wt @ y
     assert sorted(np.lexsort((np.arange(H), -raw))[:2].tolist()) != sel[2]
+
+
+# ---------------------------------------------------------------------------
+# TSC / DSC (Table 1: linear superposition, discrete latents, categorical prior)
+# ---------------------------------------------------------------------------
+DSC_VALS = np.array([0.5, 2.0, -1.5])
+DSC_P = np.array([0.15, 0.1, 0.05])
+
+
+def brute_logjoint_dsc(y, Wt, vals, pvals, sigma):
+    """log p(s, y) for every s in {0, vals}^H: categorical prior, scipy Gaussian."""
+    H, D = Wt.shape
+    levels = np.concatenate([[0.0], vals])
+    lp = np.log(np.concatenate([[1.0 - np.sum(pvals)], pvals]))
+    idx = np.array(list(itertools.product(range(len(levels)), repeat=H)))
+    S = levels[idx]
+    prior = lp[idx].sum(1)
+    ll = multivariate_normal(mean=np.zeros(D), cov=sigma ** 2 * np.eye(D)).logpdf(y[None, :] - S @ Wt)
+    return S, prior + ll
+
+
+def dsc_state_vectors(post, H, vals):
+    sel = post["sel"]
+    V = np.zeros((len(post["masks"]), H))
+    for i, (m, c) in enumerate(zip(post["masks"], post["vcodes"])):
+        a = 0
+        for j in range(len(sel)):
+            if (int(m) >> j) & 1:
+                V[i, sel[j]] = vals[(int(c) >> (2 * a)) & 3]
+                a += 1
+    return V
+
+
+def match_value_states(V, S):
+    key = {tuple(np.round(s, 12)): i for i, s in enumerate(S)}
+    return np.array([key[tuple(np.round(v, 12))] for v in V])
+
+
+def test_dsc_state_counts_golden(orc):
+    path = os.path.join(GOLDEN, "dsc_state_counts.txt")
+    rows = [l.split("#")[0].split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 5
+    for hp, g, m, n in rows:
+        assert orc.num_states_m(int(hp), int(g), int(m)) == int(n)
+        assert len(orc.states_dsc(int(hp), int(g), int(m))[0]) == int(n)
+
+
+def test_dsc_state_order_is_canonical(orc):
+    """By number of nonzero units, then the units' combination order, then the
+    value indices (itertools.product order, first unit most significant)."""
+    for hp, g, m in [(5, 3, 2), (4, 4, 3), (6, 2, 1)]:
+        masks, codes = orc.states_dsc(hp, g, m)
+        expect = []
+        for k in range(g + 1):
+            for c in itertools.combinations(range(hp), k):
+                for v in itertools.product(range(m), repeat=k):
+                    expect.append((sum(1 << j for j in c), sum(vi << (2 * a) for a, vi in enumerate(v))))
+        assert list(zip(masks.tolist(), codes.tolist())) == expect
+
+
+@pytest.mark.parametrize("model", ["TSC", "DSC"])
+def test_discrete_exact_equals_bruteforce(orc, model):
+    """ET with H' = H = gamma is exact: log-joints, posterior and log p(y) equal
+    the sum over all |Phi|^H states with scipy's Gaussian density and the
+    categorical prior (TSC: Phi = {-1, 0, 1}, p(+-1) = pi/2)."""
+    g = synth.rng(21)
+    if model == "TSC":
+        H, D, pi = 5, 7, 0.3
+        vals, pvals, kw = np.array([-1.0, 1.0]), np.array([pi / 2, pi / 2]), {}
+    else:
+        H, D, pi = 4, 6, float(DSC_P.sum())
+        vals, pvals = DSC_VALS, DSC_P
+        kw = dict(vals=vals, pvals=pvals)
+    Wt = g.standard_normal((H, D))
+    m = getattr(orc, model)
+    sigma = 0.9
+    for _ in range(3):
+        s_true = g.choice(np.concatenate([[0.0], vals]), H)
+        y = s_true @ Wt + sigma * g.standard_normal(D)
+        post = orc.posterior(m, y, Wt, pi, sigma, H, H, **kw)
+        S, lj = brute_logjoint_dsc(y, Wt, vals, pvals, sigma)
+        assert len(post["q"]) == len(S)
+        idx = match_value_states(dsc_state_vectors(post, H, vals), S)
+        assert len(set(idx.tolist())) == len(S)
+        np.testing.assert_allclose(post["ell"], lj[idx], rtol=1e-12, atol=1e-10)
+        np.testing.assert_allclose(post["q"], np.exp(lj - logsumexp(lj))[idx], rtol=1e-10, atol=1e-14)
+        out = orc.estep(m, y[None, :], Wt, pi, sigma, H, H, **kw)
+        assert abs(out["logZ"][0] - logsumexp(lj)) < 1e-10
+        # moments from the brute-force posterior
+        q = np.exp(lj - logsumexp(lj))
+        np.testing.assert_allclose(out["At"], np.outer(q @ S, y), rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(out["B"], (S * q[:, None]).T @ S, rtol=1e-10, atol=1e-12)
+
+
+def test_dsc_binary_values_reduce_to_bsc(orc):
+    """DSC with the single nonzero value 1 (probability pi) is BSC."""
+    Y, Wt = _small_bsc(8, H=8, D=9, N=5)
+    a = orc.estep(orc.DSC, Y, Wt, 0.2, 0.8, 5, 3, vals=[1.0], pvals=[0.2])
+    b = orc.estep(orc.BSC, Y, Wt, 0.2, 0.8, 5, 3)
+    for k in ("sel", "smean", "logZ", "At", "B", "map_idx"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(a["scal"][:4], b["scal"][:4], rtol=1e-12)
+
+
+def test_tsc_is_dsc_with_symmetric_values(orc):
+    Y, Wt = _small_bsc(9, H=8, D=9, N=5)
+    a = orc.estep(orc.TSC, Y, Wt, 0.2, 0.8, 5, 3)
+    b = orc.estep(orc.DSC, Y, Wt, 0.2, 0.8, 5, 3, vals=[-1.0, 1.0], pvals=[0.1, 0.1])
+    for k in ("sel", "smean", "logZ", "At", "B", "map_idx", "map_val", "scal"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-13)
+
+
+def test_tsc_selection_takes_magnitude(orc):
+    """TSC preselection (reading): |W_h^T y| / ||W_h||, so a latent that explains
+    y with the value -1 is a candidate; BSC's signed score would skip it."""
+    D = 6
+    Wt = np.eye(D)[:5] * np.array([[1.0], [2.0], [1.0], [1.0], [3.0]])
+    y = np.array([0.5, -4.0, 0.1, 1.0, 0.0, 0.0])       # scores: .5, -4, .1, 1, 0
+    tsc = orc.scores(orc.TSC, y, Wt)
+    bsc = orc.scores(orc.BSC, y, Wt)
+    np.testing.assert_array_equal(tsc, [0.5, 4.0, 0.1, 1.0, 0.0])
+    np.testing.assert_array_equal(bsc, [0.5, -4.0, 0.1, 1.0, 0.0])
+    assert orc.posterior(orc.TSC, y, Wt, 0.2, 1.0, 2, 1)["sel"].tolist() == [1, 3]
+    assert orc.posterior(orc.BSC, y, Wt, 0.2, 1.0, 2, 1)["sel"].tolist() == [0, 3]
+    # DSC with only negative values negates the score
+    neg = orc.scores(orc.DSC, y, Wt, vals=[-1.0, -2.0], pvals=[0.1, 0.1])
+    np.testing.assert_array_equal(neg, -bsc)
+
+
+def _Q_dsc(orc, model, posts, Y, Wt, sigma, vals, pvals):
+    """sum_n E_q[log p(s) + log p(y|s)] with the categorical prior and an
+    independent residual formula (q and the states from the E-step)."""
+    H, D = Wt.shape
+    lp = np.log(np.concatenate([[1 - np.sum(pvals)], pvals]))
+    Q = 0.0
+    for post, y in zip(posts, Y):
+        V = dsc_state_vectors(post, H, vals)
+        vi = np.zeros(V.shape, int)
+        for k, v in enumerate(vals):
+            vi[V == v] = k + 1
+        prior = lp[vi].sum(1)
+        r2 = ((y[None, :] - V @ Wt) ** 2).sum(1)
+        Q += post["q"] @ (prior - 0.5 * D * np.log(2 * np.pi * sigma ** 2) - r2 / (2 * sigma ** 2))
+    return Q
+
+
+def test_dsc_mstep_is_stationary_point_of_Q(orc):
+    """The DSC M-step (W = A B^-1, sigma^2, each value's probability = its
+    expected frequency) zeroes the gradient of Q, including along the simplex
+    directions of the categorical prior."""
+    g = synth.rng(31)
+    H, D, N = 6, 8, 40
+    Wt0 = g.standard_normal((H, D))
+    S = g.choice(np.concatenate([[0.0], DSC_VALS]), (N, H), p=[0.7, 0.15, 0.1, 0.05])
+    Y = S @ Wt0 + 0.7 * g.standard_normal((N, D))
+    Wt = Wt0 + 0.3 * g.standard_normal((H, D))
+    kw = dict(vals=DSC_VALS, pvals=DSC_P)
+    Hp, gam = 4, 2
+    out = orc.estep(orc.DSC, Y, Wt, DSC_P.sum(), 0.8, Hp, gam, **kw)
+    posts = [orc.posterior(orc.DSC, y, Wt, DSC_P.sum(), 0.8, Hp, gam, **kw) for y in Y]
+    W2, pi2, s2, p2 = orc.mstep_dsc(orc.DSC, N, out, Wt, DSC_P.sum(), 0.8, **kw)
+    assert abs(pi2 - p2.sum()) < 1e-12
+    Q = lambda W, s, p: _Q_dsc(orc, orc.DSC, posts, Y, W, s, DSC_VALS, p)
+    base = Q(W2, s2, p2)
+    eps = 1e-5
+    for (h, dd) in [(0, 0), (2, 5), (5, 7)]:
+        Wp, Wm = W2.copy(), W2.copy()
+        Wp[h, dd] += eps
+        Wm[h, dd] -= eps
+        assert abs((Q(Wp, s2, p2) - Q(Wm, s2, p2)) / (2 * eps)) < 1e-6 * abs(base)
+    assert abs((Q(W2, s2 + eps, p2) - Q(W2, s2 - eps, p2)) / (2 * eps)) < 1e-6 * abs(base)
+    for v in range(3):          # moving mass between value v and 0 (pi_0 absorbs it)
+        e = np.zeros(3)
+        e[v] = eps
+        assert abs((Q(W2, s2, p2 + e) - Q(W2, s2, p2 - e)) / (2 * eps)) < 1e-6 * abs(base), v
+    assert Q(W2, s2, p2 * 1.1) < base and Q(W2 * 1.01, s2, p2) < base
+
+
+def test_tsc_exact_em_monotone(orc):
+    """Exact TSC EM (H' = H = gamma): the log-likelihood never decreases."""
+    g = synth.rng(41)
+    H, D, N = 5, 6, 80
+    Wt0 = g.standard_normal((H, D))
+    S = g.choice([-1.0, 0.0, 1.0], (N, H), p=[0.15, 0.7, 0.15])
+    Y = S @ Wt0 + 0.5 * g.standard_normal((N, D))
+    Wt, pi, sigma = g.standard_normal((H, D)), 0.5, float(Y.std())
+    F_prev = -np.inf
+    for it in range(12):
+        out = orc.estep(orc.TSC, Y, Wt, pi, sigma, H, H)
+        F = out["scal"][orc.SC_F]
+        assert F >= F_prev - 1e-9 * abs(F), (it, F, F_prev)
+        F_prev = F
+        Wt, pi, sigma, _ = orc.mstep_dsc(orc.TSC, N, out, Wt, pi, sigma)
 
 
 # ---------------------------------------------------------------------------
