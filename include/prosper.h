@@ -6,7 +6,8 @@
  * Paper: G. Exarchakis et al., "ProSper -- A Python Library for Probabilistic
  * Sparse Coding with Non-Standard Priors and Superpositions" (arXiv 1908.06843).
  *   Eq. 1-2        generative model template p(s|Theta), p(y|s,Theta) = p(y; f(Theta,s))
- *   Table 1        models: BSC (linear, binary), GSC (linear, spike-and-slab), MCA (max)
+ *   Table 1        models: BSC (linear, binary), TSC (linear, ternary), DSC (linear,
+ *                  discrete), GSC (linear, spike-and-slab), MCA (max)
  *   Sec. 2         EM with truncated posteriors
  *   Sec. 3         BSC_ET(D, H, Hprime, gamma); Model.step; Model.inference -> res["s"], res["p"]
  *
@@ -49,6 +50,10 @@ extern "C" {
 #define PROSPER_BSC 0  /* binary sparse coding: linear f = W s, s in {0,1}^H, Bernoulli(pi) prior */
 #define PROSPER_MCA 1  /* maximal causes analysis: f_d = max_h W_dh s_h, W >= 0 */
 #define PROSPER_GSC 2  /* Gaussian sparse coding: s_h = b_h z_h, b ~ Bernoulli(pi), z_h ~ N(mu_h, psi_h) */
+#define PROSPER_TSC 3  /* ternary sparse coding: linear f = W s, s in {-1,0,1}^H, zero-mean categorical
+                          prior p(s_h = -1) = p(s_h = 1) = pi/2 */
+#define PROSPER_DSC 4  /* discrete sparse coding: linear f = W s, s_h in {0, phi_1 .. phi_m} (m <= 3 values
+                          fixed by prosper_init_dsc), categorical prior p(s_h = phi_v) = theta[TH_DSC_P + v] */
 
 /* Precision of the BSC preselection projection W^T y (other models: FP32 only). */
 #define PROSPER_FP32          0  /* FP32 SIMT projection; exact top-H' of the FP32 scores */
@@ -57,12 +62,22 @@ extern "C" {
                                     rounded to 15 mantissa bits (ties to the lower h); the H'
                                     selected projections are recomputed in FP32 */
 
-/* Limits.  BSC/MCA: 1 <= Hprime <= 10; GSC: Hprime <= 10 and gamma <= 3;
- * 0 <= gamma <= Hprime <= H; BSC/MCA/GSC H <= 256; D <= 1024.
- * PROSPER_BF16_RESCORE additionally needs D % 64 == 0, H % 64 == 0 and
+/* Limits (prosper_init returns PROSPER_EINVAL outside them).
+ *   all models: 0 <= gamma <= Hprime <= H, H <= 256, D <= 1024.
+ *   BSC:     1 <= Hprime <= 16, |K| <= 4096 states per point; for Hprime > 10 also
+ *            gamma <= 8 (those use the table-driven state kernel).
+ *   TSC/DSC: 1 <= Hprime <= 16, gamma <= 8, |K| = sum_{k<=gamma} C(Hprime,k) m^k <= 4096.
+ *   MCA:     1 <= Hprime <= 16, |K| <= 1024, D <= 256.
+ *   GSC:     1 <= Hprime <= 10, gamma <= 3, H <= 32, D <= 256, and the E-step's
+ *            shared memory (dictionary, Gram matrix, per-warp slots, about
+ *            4 (H D + H^2 + 8 (H D + 32 N_s + 3 H + 8 |K| + 64 + D)) bytes with
+ *            N_s = 2 Hprime + Hprime (Hprime + 1)/2) within 227 KB; e.g.
+ *            D = 64, H = 32, Hprime = 8, gamma = 3 uses 163 KB.
+ * PROSPER_BF16_RESCORE (BSC only) additionally needs D % 64 == 0, H % 64 == 0 and
  * 2*H*D + 256*max(D, H) <= 226 KB (the BF16 dictionary and one operand tile
  * stay in shared memory), e.g. D = H = 256. */
-#define PROSPER_MAX_HPRIME 10
+#define PROSPER_MAX_HPRIME 16
+#define PROSPER_MAX_STATES 4096
 
 /* theta[] layout (device doubles, PROSPER_THETA_LEN of them). */
 #define PROSPER_TH_PI    0   /* prior activation probability pi                   */
@@ -74,7 +89,10 @@ extern "C" {
                                 log Z_n = T log sum_{s in K_n} p(s, y_n)^(1/T);
                                 a value <= 0 is read as T = 1 (no annealing).
                                 The M-step does not read or change it. */
-#define PROSPER_THETA_LEN 4
+#define PROSPER_TH_DSC_P 4   /* DSC: prior probabilities of the m nonzero values, theta[4 .. 4+m-1]
+                                (p(s_h = 0) = 1 - their sum); the M-step updates them and sets
+                                theta[TH_PI] to their sum.  Other models read 4 doubles only. */
+#define PROSPER_THETA_LEN 8
 
 /* scal[] layout of the scalar sufficient statistics (device doubles). */
 #define PROSPER_SC_F      0  /* F = sum_n log sum_{s in K_n} p(s, y_n | Theta) (truncated log-likelihood, nats) */
@@ -82,6 +100,7 @@ extern "C" {
 #define PROSPER_SC_YY     2  /* sum_n y_n^T y_n                                                          */
 #define PROSPER_SC_N      3  /* number of points accumulated                                             */
 #define PROSPER_SC_MCA_R2 4  /* MCA: sum_n <||y_n - f(s)||^2>  (hard max, current W)                     */
+#define PROSPER_SC_DSC0   5  /* TSC/DSC: scal[5 + v] = sum_n sum_h <[s_h = phi_{v+1}]> (value counts)    */
 #define PROSPER_SC_LEN    8
 
 typedef struct prosper_ctx prosper_ctx;
@@ -89,7 +108,7 @@ typedef struct prosper_ctx prosper_ctx;
 /* Model parameters Theta (Eq. 1-2).  All device pointers. */
 typedef struct {
     float  *W;      /* H x D row-major FP32; read by E-step/encode, overwritten by M-step */
-    double *theta;  /* PROSPER_THETA_LEN doubles: pi, sigma, rho                          */
+    double *theta;  /* pi, sigma, rho, T (+ DSC value probabilities): see PROSPER_TH_*    */
     float  *mu;     /* GSC: H slab means (NULL for BSC/MCA)                               */
     float  *psi;    /* GSC: H slab variances (NULL for BSC/MCA)                           */
 } prosper_params;
@@ -113,6 +132,16 @@ typedef struct {
 int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gamma,
                  int precision, int64_t max_points);
 
+/* Context for DSC (Table 1, row DSC: linear superposition, discrete latents,
+ * categorical prior) with the m (1..3) nonzero latent values values_host[0..m-1]
+ * (host array, distinct and nonzero; copied).  The state set holds every pattern
+ * of at most gamma nonzero units among the Hprime candidates, each taking one of
+ * the m values; the preselection score is sign(phi) W_h^T y/||W_h|| maximised
+ * over the values (|W_h^T y|/||W_h|| when the values have both signs).
+ * FP32 only; otherwise as prosper_init. */
+int prosper_init_dsc(prosper_ctx **out, int D, int H, int Hprime, int gamma, int m,
+                     const float *values_host, int64_t max_points);
+
 /* Release the context and everything it allocated.  NULL is accepted. */
 int prosper_destroy(prosper_ctx *ctx);
 
@@ -122,13 +151,15 @@ int prosper_destroy(prosper_ctx *ctx);
  * is evaluated, the posterior over that set is normalised, and the
  * sufficient statistics are summed into *out (overwritten).
  * Y: device N x D FP32.  N >= 0 (N = 0 gives zero statistics).
- * Selection scores: BSC W_h^T y/||W_h||; MCA sum_d W_dh y_d / sum_d W_dh;
- * GSC the singleton log-joint log p(e_h, y).  Exact score ties go to the lower h. */
+ * Selection scores: BSC W_h^T y/||W_h||; TSC |W_h^T y|/||W_h||; DSC see
+ * prosper_init_dsc; MCA sum_d W_dh y_d / sum_d W_dh; GSC the singleton
+ * log-joint log p(e_h, y).  Exact score ties go to the lower h. */
 int prosper_estep(prosper_ctx *ctx, const prosper_params *p, const float *Y, int64_t N,
                   prosper_stats *out, void *stream);
 
 /* Closed-form M-step ("Model.step", Sec. 3) from statistics of N points:
- * BSC/GSC W = A B^{-1} (FP64, blocked Cholesky of B), pi = sum<|s|>/(N H),
+ * BSC/TSC/DSC/GSC W = A B^{-1} (FP64, blocked Cholesky of B), pi = sum<|s|>/(N H)
+ * (TSC: p(+-1) = pi/2; DSC: theta[TH_DSC_P + v] = scal[SC_DSC0 + v]/(N H)),
  * sigma^2 = (sum y^T y - 2 tr(W^T A) + tr(W^T W B))/(N D) with the new W;
  * GSC also mu_h, psi_h; MCA the rho-smoothed-max update of W (clamped >= 1e-6),
  * pi as BSC, sigma^2 = sum<||y - f||^2>/(N D).  A unit with B_hh <= 1e-9 N
@@ -148,6 +179,15 @@ int prosper_mstep(prosper_ctx *ctx, const prosper_stats *st, int64_t N, prosper_
 int prosper_encode(prosper_ctx *ctx, const prosper_params *p, const float *Y, int64_t N,
                    int16_t *sel, float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
                    void *stream);
+
+/* prosper_encode for the discrete-latent models (TSC, DSC), which also writes
+ * map_val (N x gamma float, may be NULL): the value of each unit listed in
+ * map_idx (0 where map_idx is -1).  s_mean then holds the signed posterior means
+ * <s_h>.  PROSPER_EINVAL for the other models (their MAP units all take the
+ * value 1). */
+int prosper_encode_values(prosper_ctx *ctx, const prosper_params *p, const float *Y, int64_t N,
+                          int16_t *sel, float *s_mean, int16_t *map_idx, float *map_val,
+                          float *map_p, float *logZ, void *stream);
 
 /* BSC encoding without any device allocation (the paper has no counterpart:
  * this serves callers that cannot call cudaMalloc when they encode -- code

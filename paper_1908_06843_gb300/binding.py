@@ -16,11 +16,11 @@ import numpy as np
 
 from . import build as _build
 
-BSC, MCA, GSC = 0, 1, 2
+BSC, MCA, GSC, TSC, DSC = 0, 1, 2, 3, 4
 FP32, BF16_RESCORE = 0, 1
-TH_PI, TH_SIGMA, TH_RHO, THETA_LEN = 0, 1, 2, 4
-SC_F, SC_S1, SC_YY, SC_N, SC_MCA_R2, SC_LEN = 0, 1, 2, 3, 4, 8
-MAX_HPRIME = 10
+TH_PI, TH_SIGMA, TH_RHO, TH_T, TH_DSC_P, THETA_LEN = 0, 1, 2, 3, 4, 8
+SC_F, SC_S1, SC_YY, SC_N, SC_MCA_R2, SC_DSC0, SC_LEN = 0, 1, 2, 3, 4, 5, 8
+MAX_HPRIME, MAX_STATES = 16, 4096
 
 # function name -> (restype, argtypes); the list is the exported C ABI
 _P = ctypes.c_void_p
@@ -28,6 +28,8 @@ _I = ctypes.c_int
 _I64 = ctypes.c_int64
 ABI = {
     "prosper_init": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _I, _I64]),
+    "prosper_init_dsc": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _P, _I64]),
+    "prosper_encode_values": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "prosper_destroy": (_I, [_P]),
     "prosper_estep": (_I, [_P, _P, _P, _I64, _P, _P]),
     "prosper_mstep": (_I, [_P, _P, _I64, _P, _P]),
@@ -113,15 +115,24 @@ def _require_cuda(*ts):
 
 class Context:
     """Owns a prosper_ctx (one model and approximation, paper Sec. 3:
-    BSC_ET(D, H, Hprime, gamma))."""
+    BSC_ET(D, H, Hprime, gamma)).  DSC contexts take ``values``: the m <= 3
+    nonzero latent values (prosper_init_dsc)."""
 
-    def __init__(self, model, D, H, Hprime, gamma, precision=FP32, max_points=1 << 20):
+    def __init__(self, model, D, H, Hprime, gamma, precision=FP32, max_points=1 << 20,
+                 values=None):
         self.lib = load()
         self.model, self.D, self.H, self.Hp, self.gamma = model, D, H, Hprime, gamma
         self.precision = precision
         h = _P()
-        _check(self.lib.prosper_init(ctypes.byref(h), model, D, H, Hprime, gamma, precision,
-                                     int(max_points)), "prosper_init")
+        if model == DSC:
+            vals = np.ascontiguousarray(values, np.float32)
+            self.values = vals
+            _check(self.lib.prosper_init_dsc(ctypes.byref(h), D, H, Hprime, gamma, len(vals),
+                                             _ptr(vals), int(max_points)), "prosper_init_dsc")
+        else:
+            self.values = np.array([-1.0, 1.0] if model == TSC else [1.0], np.float32)
+            _check(self.lib.prosper_init(ctypes.byref(h), model, D, H, Hprime, gamma, precision,
+                                         int(max_points)), "prosper_init")
         self.h = h
 
     def close(self):
@@ -137,8 +148,12 @@ class Context:
 
     # -------------------------------------------------------------- helpers
     def params(self, W, theta, mu=None, psi=None) -> Params:
+        """prosper_params pointing at these device tensors.  The struct keeps
+        references to them, so they stay allocated while it is in use."""
         _require_cuda(W, theta, mu, psi)
-        return Params(_ptr(W), _ptr(theta), _ptr(mu), _ptr(psi))
+        P = Params(_ptr(W), _ptr(theta), _ptr(mu), _ptr(psi))
+        P._tensors = (W, theta, mu, psi)
+        return P
 
     def alloc_stats(self, device="cuda"):
         import torch
@@ -169,9 +184,12 @@ class Context:
                                       _stream(stream)), "prosper_mstep")
 
     def encode(self, P: Params, Y, out=None, stream=None):
+        """Per-point encoding (prosper_encode; TSC/DSC: prosper_encode_values,
+        which adds map_val, the values of the MAP state's units)."""
         import torch
         _require_cuda(Y)
         N = int(Y.shape[0])
+        discrete = self.model in (TSC, DSC)
         if out is None:
             dev = Y.device
             out = dict(sel=torch.empty(N, self.Hp, dtype=torch.int16, device=dev),
@@ -179,9 +197,18 @@ class Context:
                        map_idx=torch.empty(N, self.gamma, dtype=torch.int16, device=dev),
                        map_p=torch.empty(N, dtype=torch.float32, device=dev),
                        logZ=torch.empty(N, dtype=torch.float32, device=dev))
+            if discrete:
+                out["map_val"] = torch.empty(N, self.gamma, dtype=torch.float32, device=dev)
+        g = self.gamma > 0
+        if discrete:
+            _check(self.lib.prosper_encode_values(
+                self.h, ctypes.byref(P), _ptr(Y), N, _ptr(out["sel"]), _ptr(out["s_mean"]),
+                _ptr(out["map_idx"]) if g else None, _ptr(out["map_val"]) if g else None,
+                _ptr(out["map_p"]), _ptr(out["logZ"]), _stream(stream)), "prosper_encode_values")
+            return out
         _check(self.lib.prosper_encode(self.h, ctypes.byref(P), _ptr(Y), N, _ptr(out["sel"]),
                                        _ptr(out["s_mean"]),
-                                       _ptr(out["map_idx"]) if self.gamma > 0 else None,
+                                       _ptr(out["map_idx"]) if g else None,
                                        _ptr(out["map_p"]), _ptr(out["logZ"]), _stream(stream)),
                "prosper_encode")
         return out

@@ -3,6 +3,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -63,11 +64,12 @@ TraceScope::~TraceScope() {
     if (on) cudaEventRecord(c->trace->recs[idx].b, s);
 }
 
-int num_states(int Hp, int gamma) {
-    double c = 0.0, b = 1.0;
+int num_states(int Hp, int gamma, int m) {
+    double c = 0.0, b = 1.0, mk = 1.0;
     for (int k = 0; k <= gamma && k <= Hp; ++k) {
-        c += b;
+        c += b * mk;
         b = b * (Hp - k) / (k + 1);
+        mk *= m;
     }
     return (int)(c + 0.5);
 }
@@ -125,7 +127,7 @@ static int estep_begin(prosper_ctx *c, const prosper_params *p, prosper_stats *s
         PROSPER_CUDA_TRY(cudaMemsetAsync(st->gsc, 0, sizeof(double) * 3 * H, s));
     if (c->model == PROSPER_MCA)
         PROSPER_CUDA_TRY(cudaMemsetAsync(st->mca, 0, sizeof(double) * 2 * H * D, s));
-    if (c->model == PROSPER_BSC) return launch_bsc_prep(c, p->W, s);
+    if (linear_model(c->model)) return launch_bsc_prep(c, p->W, s);
     if (c->model == PROSPER_MCA) return launch_mca_prep(c, p->W, s);
     return launch_gsc_prep(c, p, s);
 }
@@ -133,11 +135,11 @@ static int estep_begin(prosper_ctx *c, const prosper_params *p, prosper_stats *s
 static int estep_piece(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t n,
                        prosper_stats *st, cudaStream_t s) {
     int rc;
-    if (c->model == PROSPER_BSC) {
-        rc = (c->precision == PROSPER_BF16_RESCORE) ? launch_bsc_proj_bf16(c, Y, p->W, n, s)
-                                                     : launch_bsc_proj_f32(c, Y, n, s);
+    if (linear_model(c->model)) {
+        rc = launch_linear_proj(c, Y, p->W, n, s);
         if (rc) return rc;
-        rc = launch_bsc_states(c, p->theta, n, 0, st, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+        rc = launch_linear_states(c, p->theta, n, 0, st, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  nullptr, s);
         if (rc) return rc;
         return launch_astat(c, Y, n, st->At, s);
     }
@@ -161,27 +163,44 @@ extern "C" {
 
 const char *prosper_last_error(void) { return g_err; }
 
-int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gamma,
-                 int precision, int64_t max_points) {
+static int init_common(prosper_ctx **out, int model, int D, int H, int Hprime, int gamma,
+                       int precision, int64_t max_points, int m, const float *vals) {
     if (!out) { set_error("out is NULL"); return PROSPER_EINVAL; }
     *out = nullptr;
-    if (model < PROSPER_BSC || model > PROSPER_GSC) { set_error("unknown model %d", model); return PROSPER_EINVAL; }
     if (D < 1 || D > 1024) { set_error("D=%d outside [1, 1024]", D); return PROSPER_EINVAL; }
     if (H < 1 || H > 256) { set_error("H=%d outside [1, 256]", H); return PROSPER_EINVAL; }
-    if (Hprime < 1 || Hprime > PROSPER_MAX_HPRIME || Hprime > H) {
-        set_error("Hprime=%d outside [1, min(H, %d)]", Hprime, PROSPER_MAX_HPRIME);
+    const int hp_max = model == PROSPER_GSC ? BSC_REG_MAX_HPRIME : PROSPER_MAX_HPRIME;
+    if (Hprime < 1 || Hprime > hp_max || Hprime > H) {
+        set_error("Hprime=%d outside [1, min(H, %d)]", Hprime, hp_max);
         return PROSPER_EINVAL;
     }
     if (gamma < 0 || gamma > Hprime) { set_error("gamma=%d outside [0, Hprime]", gamma); return PROSPER_EINVAL; }
+    const int nK = num_states(Hprime, gamma, m);
     if (model == PROSPER_GSC && gamma > 3) { set_error("GSC: gamma=%d > 3", gamma); return PROSPER_EINVAL; }
     if (model == PROSPER_GSC && H > 32) { set_error("GSC: H=%d > 32", H); return PROSPER_EINVAL; }
     if ((model == PROSPER_GSC || model == PROSPER_MCA) && D > 256) {
         set_error("MCA/GSC: D=%d > 256", D);
         return PROSPER_EINVAL;
     }
-    if (model == PROSPER_GSC && gsc_smem_bytes(D, H, Hprime, num_states(Hprime, gamma)) > 227 * 1024) {
+    if (model == PROSPER_GSC && gsc_smem_bytes(D, H, Hprime, nK) > 227 * 1024) {
         set_error("GSC: D=%d, H=%d, Hprime=%d, gamma=%d need %zu bytes of shared memory per CTA (> 227 KB)",
-                  D, H, Hprime, gamma, gsc_smem_bytes(D, H, Hprime, num_states(Hprime, gamma)));
+                  D, H, Hprime, gamma, gsc_smem_bytes(D, H, Hprime, nK));
+        return PROSPER_EINVAL;
+    }
+    if (model == PROSPER_MCA && nK > 1024) {
+        set_error("MCA: %d states per point > 1024", nK);
+        return PROSPER_EINVAL;
+    }
+    // the table-driven state kernel (TSC, DSC, BSC above Hprime 10) packs at
+    // most 8 nonzero units per state
+    const bool table = model == PROSPER_TSC || model == PROSPER_DSC ||
+                       (model == PROSPER_BSC && Hprime > BSC_REG_MAX_HPRIME);
+    if (linear_model(model) && nK > PROSPER_MAX_STATES) {
+        set_error("%d states per point > %d", nK, PROSPER_MAX_STATES);
+        return PROSPER_EINVAL;
+    }
+    if (table && gamma > 8) {
+        set_error("gamma=%d > 8 (discrete latents, or BSC with Hprime > %d)", gamma, BSC_REG_MAX_HPRIME);
         return PROSPER_EINVAL;
     }
     if (precision != PROSPER_FP32 && precision != PROSPER_BF16_RESCORE) {
@@ -204,7 +223,17 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     if (!c) { set_error("host allocation failed"); return PROSPER_ENOMEM; }
     c->model = model; c->D = D; c->H = H; c->Hp = Hprime; c->gamma = gamma;
     c->precision = precision;
-    c->nK = num_states(Hprime, gamma);
+    c->nK = nK;
+    c->dsc_m = m;
+    bool pos = false, neg = false;
+    for (int v = 0; v < m; ++v) {
+        c->dsc_vals[v] = vals[v];
+        pos |= vals[v] > 0.f;
+        neg |= vals[v] < 0.f;
+    }
+    // preselection score: signed normalised projection; magnitude when the
+    // latent values have both signs; negated when they are all negative
+    c->score_mode = (pos && neg) ? 1 : (neg ? 2 : 0);
     c->chunk = max_points;
     c->tc_test_no_commit_ms = (test_ms > 0 && test_ms <= 2000) ? test_ms : 0;
     if (const char *e = getenv("PROSPER_ASTAT_SIMT")) c->astat_simt = atoi(e) != 0;
@@ -219,7 +248,7 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     const size_t ch = (size_t)c->chunk;
 #define ALLOC(ptr, n) do { if (!rc) rc = dev_alloc(&(ptr), (n)); } while (0)
     ALLOC(c->d_status, 1);
-    if (model == PROSPER_BSC || model == PROSPER_GSC) {
+    if (linear_model(model) || model == PROSPER_GSC) {
         ALLOC(c->G, (size_t)H * H);
         ALLOC(c->rnorm, (size_t)H);
         const size_t Hq = (size_t)mstep_hq(H);
@@ -232,7 +261,7 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
         ALLOC(c->mW, (size_t)H * D);
         ALLOC(c->mpart, (size_t)mstep_nparts(H, D));
     }
-    if (model == PROSPER_BSC) {
+    if (linear_model(model)) {
         if (precision == PROSPER_FP32) ALLOC(c->Wd, (size_t)D * H);
         else ALLOC(c->Wb, (size_t)H * D);
         ALLOC(c->sel, ch * SEL_STRIDE);
@@ -253,6 +282,7 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
         ALLOC(c->gsc_tab, (size_t)nsub * 8);
     }
 #undef ALLOC
+    if (!rc && table) rc = dsc_build_table(c);
     if (!rc && cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) rc = PROSPER_ECUDA;
     if (rc) {
         prosper_destroy(c);
@@ -260,6 +290,35 @@ int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gam
     }
     *out = c;
     return PROSPER_OK;
+}
+
+int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gamma,
+                 int precision, int64_t max_points) {
+    if (out) *out = nullptr;
+    if (model < PROSPER_BSC || model > PROSPER_TSC) {
+        set_error(model == PROSPER_DSC ? "DSC contexts are created by prosper_init_dsc"
+                                       : "unknown model %d", model);
+        return PROSPER_EINVAL;
+    }
+    static const float kBinary[1] = {1.f}, kTernary[2] = {-1.f, 1.f};
+    if (model == PROSPER_TSC)
+        return init_common(out, model, D, H, Hprime, gamma, precision, max_points, 2, kTernary);
+    return init_common(out, model, D, H, Hprime, gamma, precision, max_points, 1, kBinary);
+}
+
+int prosper_init_dsc(prosper_ctx **out, int D, int H, int Hprime, int gamma, int m,
+                     const float *values_host, int64_t max_points) {
+    if (out) *out = nullptr;
+    if (m < 1 || m > 3 || !values_host) { set_error("DSC: m=%d outside [1, 3] or no values", m); return PROSPER_EINVAL; }
+    for (int v = 0; v < m; ++v) {
+        if (!(values_host[v] != 0.f) || !std::isfinite(values_host[v])) {
+            set_error("DSC: value %d is zero or not finite", v);
+            return PROSPER_EINVAL;
+        }
+        for (int u = 0; u < v; ++u)
+            if (values_host[u] == values_host[v]) { set_error("DSC: values %d and %d are equal", u, v); return PROSPER_EINVAL; }
+    }
+    return init_common(out, PROSPER_DSC, D, H, Hprime, gamma, PROSPER_FP32, max_points, m, values_host);
 }
 
 int prosper_status(prosper_ctx *c, void *stream) {
@@ -324,7 +383,7 @@ int prosper_destroy(prosper_ctx *c) {
     }
     cudaFree(c->d_hstats);
     cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
-    cudaFree(c->mca_logW); cudaFree(c->gsc_tab);
+    cudaFree(c->mca_logW); cudaFree(c->gsc_tab); cudaFree(c->dsc_tab);
     cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es); cudaFree(c->apart);
     if (c->h_copy) {
         cudaStreamSynchronize(c->h_copy);
@@ -365,24 +424,23 @@ int prosper_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_pa
     return launch_mstep(c, st, N, p, (cudaStream_t)stream);
 }
 
-int prosper_encode(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
-                   int16_t *sel, float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
-                   void *stream) {
+static int encode_impl(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
+                       int16_t *sel, float *s_mean, int16_t *map_idx, float *map_val, float *map_p,
+                       float *logZ, void *stream) {
     if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
     int rc = check_params(c, p);
     if (rc) return rc;
     if (N < 0 || (N > 0 && !Y)) { set_error("bad Y/N"); return PROSPER_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     if (N == 0) return PROSPER_OK;
-    if (c->model == PROSPER_BSC) {
+    if (linear_model(c->model)) {
         if ((rc = launch_bsc_prep(c, p->W, s))) return rc;
         for (int64_t n0 = 0; n0 < N; n0 += c->chunk) {
             const int64_t n = std::min<int64_t>(c->chunk, N - n0);
             const float *Yp = Y + n0 * c->D;
-            rc = (c->precision == PROSPER_BF16_RESCORE) ? launch_bsc_proj_bf16(c, Yp, p->W, n, s)
-                                                         : launch_bsc_proj_f32(c, Yp, n, s);
-            if (rc) return rc;
-            rc = launch_bsc_states(c, p->theta, n, n0, nullptr, sel, s_mean, map_idx, map_p, logZ, s);
+            if ((rc = launch_linear_proj(c, Yp, p->W, n, s))) return rc;
+            rc = launch_linear_states(c, p->theta, n, n0, nullptr, sel, s_mean, map_idx, map_val,
+                                      map_p, logZ, s);
             if (rc) return rc;
         }
         return PROSPER_OK;
@@ -394,6 +452,22 @@ int prosper_encode(prosper_ctx *c, const prosper_params *p, const float *Y, int6
     }
     if ((rc = launch_gsc_prep(c, p, s))) return rc;
     return launch_gsc_estep(c, p, Y, N, nullptr, sel, s_mean, map_idx, map_p, logZ, s);
+}
+
+int prosper_encode(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
+                   int16_t *sel, float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
+                   void *stream) {
+    return encode_impl(c, p, Y, N, sel, s_mean, map_idx, nullptr, map_p, logZ, stream);
+}
+
+int prosper_encode_values(prosper_ctx *c, const prosper_params *p, const float *Y, int64_t N,
+                          int16_t *sel, float *s_mean, int16_t *map_idx, float *map_val,
+                          float *map_p, float *logZ, void *stream) {
+    if (c && c->model != PROSPER_TSC && c->model != PROSPER_DSC) {
+        set_error("encode_values: TSC or DSC contexts only");
+        return PROSPER_EINVAL;
+    }
+    return encode_impl(c, p, Y, N, sel, s_mean, map_idx, map_val, map_p, logZ, stream);
 }
 
 int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_host, int64_t N,

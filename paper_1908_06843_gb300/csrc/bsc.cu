@@ -99,7 +99,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // other shared-memory stage (cp.async).
 __global__ void __launch_bounds__(256, 1)
 k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
-               const float *__restrict__ rnorm, int64_t N, int D, int H, int Hp,
+               const float *__restrict__ rnorm, int64_t N, int D, int H, int Hp, int score_mode,
                int32_t *__restrict__ sel_out, float *__restrict__ selp_out,
                float2 *__restrict__ yy_out, unsigned *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -113,12 +113,16 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
     const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
     const int64_t nq = my_tiles * nk;   // chunks this CTA processes
 
+    // score = sign * P_h / ||W_h||; score_mode 1 (discrete latents with values
+    // of both signs) ranks by magnitude instead
+    const float sgn = score_mode == 2 ? -1.f : 1.f;
+    const bool mag = score_mode == 1;
     float rn[8];
     unsigned kmask[8], klow[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int h = lane + 32 * j;
-        rn[j] = h < H ? rnorm[h] : 0.f;
+        rn[j] = h < H ? sgn * rnorm[h] : 0.f;
         kmask[j] = h < H ? 0xFFFFFF00u : 0u;
         klow[j] = h < H ? (unsigned)(255 - h) : 0u;
     }
@@ -259,14 +263,16 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
             // the exact selection below decides.
             unsigned pk[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                pk[j] = packed_key(kmask[j] ? sm.Ps[p][lane + 32 * j] * rn[j] : 0.f, kmask[j], klow[j]);
+            for (int j = 0; j < 8; ++j) {
+                const float sc = kmask[j] ? sm.Ps[p][lane + 32 * j] * rn[j] : 0.f;
+                pk[j] = packed_key(mag ? fabsf(sc) : sc, kmask[j], klow[j]);
+            }
             sort8_desc(pk);
             int myh = 0x7fffffff;
             unsigned wlast = 0u, wnext = 0u;
 #pragma unroll
             for (int r = 0; r <= PROSPER_MAX_HPRIME; ++r) {
-                if (r <= Hp) {
+                if (r <= Hp) {   // warp-uniform
                     const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
                     if (lane == r && r < Hp) myh = 255 - (int)(w & 0xFFu);
                     if (r == Hp - 1) wlast = w;
@@ -283,7 +289,8 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     int h = lane + 32 * j;
-                    key[j] = h < H ? score_key(sm.Ps[p][h] * rn[j]) : 0u;
+                    const float sc = sm.Ps[p][lane + 32 * j] * rn[j];
+                    key[j] = h < H ? score_key(mag ? fabsf(sc) : sc) : 0u;
                 }
                 myh = warp_topk(key, Hp, lane, sm.topk[warp]);
             }
@@ -833,8 +840,9 @@ int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t 
     int64_t ntiles = (N + PT - 1) / PT;
     int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_f32", s);
-    k_bsc_proj_f32<<<grid, 256, smem, s>>>(Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->sel,
-                                           c->selp, reinterpret_cast<float2 *>(c->yy), c->d_status);
+    k_bsc_proj_f32<<<grid, 256, smem, s>>>(Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->score_mode,
+                                           c->sel, c->selp, reinterpret_cast<float2 *>(c->yy),
+                                           c->d_status);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }

@@ -234,23 +234,28 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                     for (int c = lane; c < nchunk; c += 32) {
                         const float4 y0 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c));
                         const float4 y1 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c + 4));
-                        // all row loads first (always in bounds), then the dot products
-                        float4 w[2 * PROSPER_MAX_HPRIME];
+                        // rows in batches of 8: all of a batch's row loads first
+                        // (always in bounds), then its dot products
 #pragma unroll
-                        for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                            const float *wrow = Wt + (size_t)hsel[r] * D + 8 * c;
-                            w[2 * r] = __ldg(reinterpret_cast<const float4 *>(wrow));
-                            w[2 * r + 1] = __ldg(reinterpret_cast<const float4 *>(wrow + 4));
-                        }
+                        for (int rb = 0; rb < PROSPER_MAX_HPRIME; rb += 8) {
+                            if (rb >= Hp) break;   // warp-uniform
+                            float4 w[16];
 #pragma unroll
-                        for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                            const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
-                            float s = v[r];
-                            s = fmaf(y0.x, w0.x, s); s = fmaf(y0.y, w0.y, s);
-                            s = fmaf(y0.z, w0.z, s); s = fmaf(y0.w, w0.w, s);
-                            s = fmaf(y1.x, w1.x, s); s = fmaf(y1.y, w1.y, s);
-                            s = fmaf(y1.z, w1.z, s); s = fmaf(y1.w, w1.w, s);
-                            v[r] = (r < Hp) ? s : 0.f;
+                            for (int r = 0; r < 8; ++r) {
+                                const float *wrow = Wt + (size_t)hsel[rb + r] * D + 8 * c;
+                                w[2 * r] = __ldg(reinterpret_cast<const float4 *>(wrow));
+                                w[2 * r + 1] = __ldg(reinterpret_cast<const float4 *>(wrow + 4));
+                            }
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) {
+                                const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
+                                float s = v[rb + r];
+                                s = fmaf(y0.x, w0.x, s); s = fmaf(y0.y, w0.y, s);
+                                s = fmaf(y0.z, w0.z, s); s = fmaf(y0.w, w0.w, s);
+                                s = fmaf(y1.x, w1.x, s); s = fmaf(y1.y, w1.y, s);
+                                s = fmaf(y1.z, w1.z, s); s = fmaf(y1.w, w1.w, s);
+                                v[rb + r] = (rb + r < Hp) ? s : 0.f;
+                            }
                         }
                     }
 #pragma unroll

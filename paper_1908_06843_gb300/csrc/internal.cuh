@@ -21,9 +21,15 @@ void set_error(const char *fmt, ...);
 // changes).  Returns PROSPER_OK or PROSPER_ECUDA (with set_error).
 int ensure_smem_attr(const void *func, size_t bytes);
 
-// |K| = sum_{k <= gamma} C(Hp, k): binary states with at most gamma active units
-// among Hp candidates.
-int num_states(int Hp, int gamma);
+// |K| = sum_{k <= gamma} C(Hp, k) m^k: states with at most gamma nonzero units
+// among Hp candidates, each taking one of m values (m = 1: binary latents).
+int num_states(int Hp, int gamma, int m = 1);
+
+// the linear-superposition models (BSC, TSC, DSC) share the projection,
+// preselection and sum y<s>^T kernels
+inline bool linear_model(int model) {
+    return model == PROSPER_BSC || model == PROSPER_TSC || model == PROSPER_DSC;
+}
 
 #define PROSPER_CUDA_TRY(expr)                                                     \
     do {                                                                           \
@@ -45,8 +51,11 @@ int num_states(int Hp, int gamma);
         }                                                                          \
     } while (0)
 
-// Per-point scratch rows are padded to this many entries (Hprime <= 10).
+// Per-point scratch rows are padded to this many entries (Hprime <= 16).
 constexpr int SEL_STRIDE = 16;
+// Hprime range of the register-resident BSC state kernel (k_bsc_states); above
+// it BSC uses the table-driven kernel of dsc.cu.
+constexpr int BSC_REG_MAX_HPRIME = 10;
 
 // Status word bits written by kernels (ctx->d_status).
 constexpr unsigned ST_NONFINITE = 1u;     // a data point had a non-finite y^T y
@@ -83,6 +92,10 @@ struct prosper_ctx {
     float *mca_logW = nullptr;  // MCA: H x D log W_dh
     float *gsc_tab = nullptr;   // GSC: per active subset {logdet, M_b^-1 packed} (8 floats)
     int gsc_nsub = 0;
+    void *dsc_tab = nullptr;    // table-driven state kernel: nK packed states (uint2 each)
+    int dsc_m = 1;              // nonzero latent values: 1 (binary), 2 (TSC), 1..3 (DSC)
+    float dsc_vals[3] = {1.f, 0.f, 0.f};   // the nonzero values phi_1 .. phi_m
+    int score_mode = 0;         // preselection score: 0 signed, 1 magnitude, 2 negated
 
     // per-piece scratch
     int32_t *sel = nullptr;   // chunk x SEL_STRIDE selected latents (ascending)
@@ -131,6 +144,18 @@ size_t bf16_smem_bytes(int D, int H);
 int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_offset,
                       prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
                       float *mapp_out, float *logz_out, cudaStream_t s);
+// table-driven warp-per-point state kernel (dsc.cu): TSC, DSC and BSC with Hprime > 10
+int dsc_build_table(prosper_ctx *c);
+size_t dsc_smem_bytes(int Hp, int m);
+int launch_dsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_offset,
+                      prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
+                      float *mapv_out, float *mapp_out, float *logz_out, cudaStream_t s);
+// BSC/TSC/DSC: projection + preselection of a piece of n points, then its
+// states (k_bsc_states for BSC with Hprime <= 10, else the table kernel)
+int launch_linear_proj(prosper_ctx *c, const float *Y, const float *W, int64_t n, cudaStream_t s);
+int launch_linear_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_offset,
+                         prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
+                         float *mapv_out, float *mapp_out, float *logz_out, cudaStream_t s);
 int launch_astat(prosper_ctx *c, const float *Y, int64_t N, double *At, cudaStream_t s);
 int launch_astat_tc(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s);
 int finish_astat_tc(prosper_ctx *c, double *At, cudaStream_t s);

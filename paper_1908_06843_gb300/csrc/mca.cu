@@ -74,7 +74,8 @@ __device__ __forceinline__ void two_sum_acc(float2 &acc, float v) {
 
 constexpr int KMAX = 1024;
 
-template <int DK, bool ENCODE, bool SMEM_STATS>
+// HPM: register arrays sized for Hprime <= HPM (10 or 16)
+template <int DK, bool ENCODE, bool SMEM_STATS, int HPM>
 __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
     extern __shared__ __align__(16) float sm[];
     const int D = A.D, H = A.H, Hp = A.Hp, gamma = A.gamma;
@@ -162,9 +163,9 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
         const int myh = warp_topk(key, Hp, lane, msk);   // msk doubles as scratch here
         __syncwarp();
         const int rank = topk_rank(myh, Hp, lane);
-        int I[PROSPER_MAX_HPRIME];
+        int I[HPM];
 #pragma unroll
-        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+        for (int j = 0; j < HPM; ++j) {
             // the latent with rank j (ascending h)
             const unsigned ball = __ballot_sync(0xffffffffu, lane < Hp && rank == j);
             I[j] = ball ? __shfl_sync(0xffffffffu, myh, __ffs(ball) - 1) : 0;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
                 for (int k = 0; k < DK; ++k) f[k] = 0.f;
 #pragma unroll
-                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+                for (int j = 0; j < HPM; ++j) {
                     if (!((mask >> j) & 1u)) continue;
 #pragma unroll
                     for (int k = 0; k < DK; ++k) {
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
             for (int i1 = 0; gamma >= 1 && i1 < Hp; ++i1) {
                 int g1 = 0;
 #pragma unroll
-                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) g1 = (j == i1) ? I[j] : g1;
+                for (int j = 0; j < HPM; ++j) g1 = (j == i1) ? I[j] : g1;
                 float f1[DK];
 #pragma unroll
                 for (int k = 0; k < DK; ++k) {
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
                 for (int i2 = i1 + 1; gamma >= 2 && i2 < Hp; ++i2) {
                     int g2 = 0;
 #pragma unroll
-                    for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) g2 = (j == i2) ? I[j] : g2;
+                    for (int j = 0; j < HPM; ++j) g2 = (j == i2) ? I[j] : g2;
                     float f2[DK];
 #pragma unroll
                     for (int k = 0; k < DK; ++k) {
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
                     for (int i3 = i2 + 1; gamma >= 3 && i3 < Hp; ++i3) {
                         int g3 = 0;
 #pragma unroll
-                        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) g3 = (j == i3) ? I[j] : g3;
+                        for (int j = 0; j < HPM; ++j) g3 = (j == i3) ? I[j] : g3;
                         float f3[DK];
 #pragma unroll
                         for (int k = 0; k < DK; ++k) {
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
                         for (int i4 = i3 + 1; gamma >= 4 && i4 < Hp; ++i4) {
                             int g4 = 0;
 #pragma unroll
-                            for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) g4 = (j == i4) ? I[j] : g4;
+                            for (int j = 0; j < HPM; ++j) g4 = (j == i4) ? I[j] : g4;
                             float f4[DK];
 #pragma unroll
                             for (int k = 0; k < DK; ++k) {
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
                             for (int i5 = i4 + 1; gamma >= 5 && i5 < Hp; ++i5) {
                                 int g5 = 0;
 #pragma unroll
-                                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) g5 = (j == i5) ? I[j] : g5;
+                                for (int j = 0; j < HPM; ++j) g5 = (j == i5) ? I[j] : g5;
                                 float f5[DK];
 #pragma unroll
                                 for (int k = 0; k < DK; ++k) {
@@ -286,9 +287,9 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
         if (nv & 31) flush(nv & ~31, nv & 31);
         const float m = warp_max(mloc);
         // ---- normalisation, posterior means, MAP (lanes over states)
-        float Z = 0.f, es[PROSPER_MAX_HPRIME];
+        float Z = 0.f, es[HPM];
 #pragma unroll
-        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) es[j] = 0.f;
+        for (int j = 0; j < HPM; ++j) es[j] = 0.f;
         float S1 = 0.f;
         int best = 0x7fffffff;
         for (int v = lane; v < nv; v += 32) {
@@ -298,14 +299,14 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
             Z += e;
             S1 += e * (float)__popc(mk);
 #pragma unroll
-            for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) es[j] += ((mk >> j) & 1u) ? e : 0.f;
+            for (int j = 0; j < HPM; ++j) es[j] += ((mk >> j) & 1u) ? e : 0.f;
             const int key = (__popc(mk) << 16) + 0xFFFF - (int)(__brev(mk) >> (32 - Hp));
             best = (l == m) ? min(best, key) : best;
         }
         Z = warp_sum(Z);
         S1 = warp_sum(S1);
 #pragma unroll
-        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) es[j] = warp_sum(es[j]);
+        for (int j = 0; j < HPM; ++j) es[j] = warp_sum(es[j]);
         best = __reduce_min_sync(0xffffffffu, (unsigned)best);
         const float invZ = 1.f / Z;
         const double logZ = ((double)m + (double)log2f(Z)) * (kLn2 * T) + logp00 - (double)yy * i2s2;
@@ -332,9 +333,9 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
         // ---- statistics: E||y-f||^2 and the smoothed-max factors for every
         //      state with nonzero weight (pixel-parallel, in lanes)
         float R2 = 0.f;
-        float Abar[PROSPER_MAX_HPRIME][DK];
+        float Abar[HPM][DK];
 #pragma unroll
-        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
+        for (int j = 0; j < HPM; ++j)
 #pragma unroll
             for (int k = 0; k < DK; ++k) Abar[j][k] = 0.f;
         for (int v = 0; v < nv; ++v) {
@@ -349,26 +350,26 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
                 const int d = lane + 32 * k;
                 if (d >= D) continue;
                 // log2 W_dh of the state's active units, read once
-                float lw[PROSPER_MAX_HPRIME];
+                float lw[HPM];
                 float lmax = -INFINITY;
 #pragma unroll
-                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+                for (int j = 0; j < HPM; ++j) {
                     lw[j] = ((mk >> j) & 1u) ? Ls[I[j] * D + d] : -INFINITY;
                     lmax = fmaxf(lmax, lw[j]);
                 }
                 float t = 0.f;
 #pragma unroll
-                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
+                for (int j = 0; j < HPM; ++j)
                     if ((mk >> j) & 1u) t += fast_ex2(rho * (lw[j] - lmax));
                 const float lbar = lmax + fast_lg2(t) / rho;     // log2 Wbar_d(s)
 #pragma unroll
-                for (int j = 0; j < PROSPER_MAX_HPRIME; ++j)
+                for (int j = 0; j < HPM; ++j)
                     if ((mk >> j) & 1u)
                         Abar[j][k] = fmaf(q, fast_ex2((rho - 1.f) * (lw[j] - lbar)), Abar[j][k]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < PROSPER_MAX_HPRIME; ++j) {
+        for (int j = 0; j < HPM; ++j) {
             if (j >= Hp) break;
             const int h = I[j];
 #pragma unroll
@@ -422,8 +423,13 @@ size_t mca_smem(int D, int H, int nK, bool smem_stats) {
 
 template <int DK, bool ENC, bool SS>
 int mca_launch(McaArgs &A, int grid, size_t smem, cudaStream_t s) {
-    if (int rc = ensure_smem_attr((const void *)k_mca_estep<DK, ENC, SS>, smem)) return rc;
-    k_mca_estep<DK, ENC, SS><<<grid, MW * 32, smem, s>>>(A);
+    if (A.Hp <= 10) {
+        if (int rc = ensure_smem_attr((const void *)k_mca_estep<DK, ENC, SS, 10>, smem)) return rc;
+        k_mca_estep<DK, ENC, SS, 10><<<grid, MW * 32, smem, s>>>(A);
+    } else {
+        if (int rc = ensure_smem_attr((const void *)k_mca_estep<DK, ENC, SS, 16>, smem)) return rc;
+        k_mca_estep<DK, ENC, SS, 16><<<grid, MW * 32, smem, s>>>(A);
+    }
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }

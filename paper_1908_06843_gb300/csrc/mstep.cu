@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(NT) k_theta(const double *__restrict__ scal,
                                               const double *__restrict__ B,
                                               const double *__restrict__ gsc, double *theta,
                                               float *mu, float *psi, int H, int D, double Ntot,
-                                              int model, unsigned *status) {
+                                              int model, int nvals, unsigned *status) {
     __shared__ double red[NT / 32];
     double pa = 0.0, pi = 0.0, qa = 0.0, x = 0.0, tr = 0.0;
     for (int i = threadIdx.x; i < n1; i += NT) {
@@ -374,6 +374,11 @@ __global__ void __launch_bounds__(NT) k_theta(const double *__restrict__ scal,
         }
         theta[PROSPER_TH_SIGMA] = sqrt(s2 > 0.0 ? s2 : 0.0);
         if (!isfinite(s2) || !isfinite(theta[PROSPER_TH_PI])) atomicOr(status, ST_NONFINITE);
+        // DSC: each nonzero value's probability is its expected frequency (the
+        // categorical argmax of Q); TSC keeps p(+-1) = pi/2 through pi alone
+        if (model == PROSPER_DSC)
+            for (int v = 0; v < nvals; ++v)
+                theta[PROSPER_TH_DSC_P + v] = scal[PROSPER_SC_DSC0 + v] / (Ntot * H);
     }
     if (model == PROSPER_GSC) {
         for (int h = threadIdx.x; h < H; h += NT) {
@@ -417,7 +422,7 @@ int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_par
         k_mca_w<<<c->num_sms * 4, 256, 0, s>>>(st->mca, p->W, H, D);
         PROSPER_LAUNCH_CHECK();
         k_theta<<<1, NT, 0, s>>>(st->scal, nullptr, 0, 0, nullptr, nullptr, p->theta, nullptr,
-                                 nullptr, H, D, Ntot, c->model, c->d_status);
+                                 nullptr, H, D, Ntot, c->model, 0, c->d_status);
         PROSPER_LAUNCH_CHECK();
         return PROSPER_OK;
     }
@@ -447,7 +452,7 @@ int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_par
     k_t2_inactive<<<n2, NT, 0, s>>>(c->mW, st->B, H, D, Ntot, c->mpart + 3 * n1);
     PROSPER_LAUNCH_CHECK();
     k_theta<<<1, NT, 0, s>>>(st->scal, c->mpart, n1, n2, st->B, st->gsc, p->theta, p->mu, p->psi,
-                             H, D, Ntot, c->model, c->d_status);
+                             H, D, Ntot, c->model, c->dsc_m, c->d_status);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }

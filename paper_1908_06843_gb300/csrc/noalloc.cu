@@ -97,7 +97,7 @@ extern "C" int prosper_encode_noalloc(int D, int H, int Hprime, int gamma, const
         set_error("encode_noalloc: D=%d, H=%d outside [1, %d] x [1, %d]", D, H, NA_D, NA_H);
         return PROSPER_EINVAL;
     }
-    if (Hprime < 1 || Hprime > PROSPER_MAX_HPRIME || Hprime > H || gamma < 0 || gamma > Hprime) {
+    if (Hprime < 1 || Hprime > BSC_REG_MAX_HPRIME || Hprime > H || gamma < 0 || gamma > Hprime) {
         set_error("encode_noalloc: Hprime=%d, gamma=%d outside the limits", Hprime, gamma);
         return PROSPER_EINVAL;
     }

@@ -100,12 +100,11 @@ static int launch_slot(ServeState *S, Slot &s, int n) {
     PROSPER_CUDA_TRY(cudaMemcpyAsync(s.d_y, s.h_y, sizeof(float) * (size_t)n * D,
                                      cudaMemcpyHostToDevice, st));
     int rc;
-    if (c->model == PROSPER_BSC) {
-        rc = (c->precision == PROSPER_BF16_RESCORE) ? launch_bsc_proj_bf16(c, s.d_y, p->W, n, st)
-                                                     : launch_bsc_proj_f32(c, s.d_y, n, st);
+    if (linear_model(c->model)) {
+        rc = launch_linear_proj(c, s.d_y, p->W, n, st);
         if (!rc)
-            rc = launch_bsc_states(c, p->theta, n, 0, nullptr, s.d_sel, s.d_smean, g > 0 ? s.d_map : nullptr,
-                                   s.d_mapp, s.d_logz, st);
+            rc = launch_linear_states(c, p->theta, n, 0, nullptr, s.d_sel, s.d_smean,
+                                      g > 0 ? s.d_map : nullptr, nullptr, s.d_mapp, s.d_logz, st);
     } else if (c->model == PROSPER_MCA) {
         rc = launch_mca_estep(c, p->W, p->theta, s.d_y, n, nullptr, s.d_sel, s.d_smean,
                               g > 0 ? s.d_map : nullptr, s.d_mapp, s.d_logz, st);
@@ -219,7 +218,7 @@ int prosper_serve_start(prosper_ctx *c, const prosper_params *p, int n_slots, in
     S->slots.resize(n_slots);
     // resident constants, computed once on the default stream
     int rc = PROSPER_OK;
-    if (c->model == PROSPER_BSC) rc = launch_bsc_prep(c, p->W, nullptr);
+    if (linear_model(c->model)) rc = launch_bsc_prep(c, p->W, nullptr);
     else if (c->model == PROSPER_GSC) rc = launch_gsc_prep(c, p, nullptr);
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) { set_error("serve_start: constants failed"); rc = PROSPER_ECUDA; }
     const size_t sp = (size_t)slot_points, D = c->D, Hp = c->Hp, g = c->gamma > 0 ? c->gamma : 1;
@@ -246,7 +245,7 @@ int prosper_serve_start(prosper_ctx *c, const prosper_params *p, int n_slots, in
                   cudaMallocHost(&s.h_smean, sizeof(float) * sp * Hp) == cudaSuccess &&
                   cudaMallocHost(&s.h_mapp, sizeof(float) * sp) == cudaSuccess &&
                   cudaMallocHost(&s.h_logz, sizeof(float) * sp) == cudaSuccess;
-        if (ok && c->model == PROSPER_BSC)
+        if (ok && linear_model(c->model))
             ok = cudaMalloc(&s.sub.sel, sizeof(int32_t) * sp * SEL_STRIDE) == cudaSuccess &&
                  cudaMalloc(&s.sub.selp, sizeof(float) * sp * SEL_STRIDE) == cudaSuccess &&
                  cudaMalloc(&s.sub.yy, sizeof(float) * sp * 2) == cudaSuccess;

@@ -20,6 +20,9 @@ model list fix the shapes):
 - ``gsc``:      D = 64, H = 32, W ~ N(0, 1)/sqrt(D), b_h ~ Bernoulli(3/32),
                 z_h ~ N(mu_h, psi_h = 0.5) with mu_h ~ U(-1, 1), s = b * z,
                 y = W s + N(0, 0.3^2).
+- ``discrete``: TSC / DSC data on the Gabor dictionary: s_h takes the value
+                phi_v with probability p_v (else 0), y = W s + N(0, sigma^2)
+                (TSC: values -1, +1 with pi/2 each).
 
 Dictionaries are returned as ``Wt`` (H x D, row h = dictionary element W_h).
 """
@@ -117,6 +120,20 @@ def gsc(N: int = 50_000, seed: int = 1004, D: int = 64, H: int = 32,
     S = B * Z
     Y = S @ Wt + sigma * g.standard_normal((N, D))
     return dict(Y=Y.astype(np.float32), Wt=Wt, S=S, pi=pi, sigma=sigma, mu=mu, psi=psi_v)
+
+
+def discrete(N: int = 50_000, seed: int = 1006, H: int = 64, side: int = 16,
+             vals=(-1.0, 1.0), pvals=(2.0 / 64, 2.0 / 64), sigma: float = 0.2):
+    """Linear superposition of a Gabor dictionary with discrete latents."""
+    g = rng(seed)
+    Wt = gabor_dictionary(H, side, g)
+    D = side * side
+    levels = np.concatenate([[0.0], np.asarray(vals, np.float64)])
+    probs = np.concatenate([[1.0 - float(np.sum(pvals))], np.asarray(pvals, np.float64)])
+    S = levels[g.choice(len(levels), size=(N, H), p=probs)]
+    Y = S @ Wt + sigma * g.standard_normal((N, D))
+    return dict(Y=Y.astype(np.float32), Wt=Wt, S=S, vals=np.asarray(vals, np.float64),
+                pvals=np.asarray(pvals, np.float64), sigma=sigma)
 
 
 # --------------------------------------------------------------------------

@@ -30,15 +30,17 @@ def relfro(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def check_selection(orc, model, Y, Wt, sel_gpu, Hp, tau_fn, mu=None, psi=None, pi=0.5, sigma=1.0):
-    """Return (n_differ, ok): every GPU set must be within tau of optimal."""
+def check_selection(orc, model, Y, Wt, sel_gpu, Hp, tau_fn, mu=None, psi=None, pi=0.5, sigma=1.0,
+                    **kw):
+    """Return (n_differ, bad): every GPU set must be within tau of optimal
+    (kw: DSC values / probabilities for the oracle's score)."""
     Yd = np.asarray(Y, np.float64)
     orc_sel = None
     n_diff = 0
     bad = []
     for n in range(len(Yd)):
         sg = np.sort(np.asarray(sel_gpu[n][:Hp], np.int64))
-        sc = orc.scores(model, Yd[n], Wt, pi, sigma, mu=mu, psi=psi)
+        sc = orc.scores(model, Yd[n], Wt, pi, sigma, mu=mu, psi=psi, **kw)
         order = np.lexsort((np.arange(len(sc)), -sc))
         so = np.sort(order[:Hp])
         if np.array_equal(sg, so):
@@ -62,15 +64,18 @@ U32 = 2.0 ** -24
 
 
 def loglik_scale(orc, model, y, Wt, pi, sigma, Hp, gamma, sel, **kw):
-    """Lambda_n of one point (see the tolerance list above)."""
+    """Lambda_n of one point (see the tolerance list above); at temperature T
+    the kernels round log-joints divided by T."""
     post = orc.posterior(model, y, Wt, pi, sigma, Hp, gamma, sel_in=sel, **kw)
-    rel = post["ell"] - post["ell"][0]
+    rel = (post["ell"] - post["ell"][0]) / kw.get("T", 1.0)
     return float(np.max(np.abs(rel[post["q"] > 1e-8])))
 
 
-def check_points(orc, model, Y, Wt, pi, sigma, Hp, gamma, sel, got, ref, key, **kw):
+def check_points(orc, model, Y, Wt, pi, sigma, Hp, gamma, sel, got, ref, key, scale=1.0, **kw):
     """Per-point check with the FP32 tolerances above; returns the max raw error.
-    key "logZ" uses the log Z bound, every other key the posterior bound."""
+    key "logZ" uses the log Z bound, every other key the posterior bound
+    (times ``scale``, the largest |latent value|, for posterior means of
+    discrete latents).  kw goes to the oracle (mu, psi, rho, T, vals, pvals)."""
     err = np.abs(np.asarray(got, np.float64) - np.asarray(ref, np.float64))
     if err.ndim > 1:
         err = err.max(axis=1)
@@ -83,6 +88,6 @@ def check_points(orc, model, Y, Wt, pi, sigma, Hp, gamma, sel, got, ref, key, **
                  + H * abs(np.log(1 - pi)) + lam)
             tol = ABS_POINT + 1e-6 * T
         else:
-            tol = ABS_POINT + 8 * U32 * lam
+            tol = (ABS_POINT + 8 * U32 * lam) * scale
         assert err[n] <= tol, (key, n, err[n], tol, lam)
     return float(err.max()) if len(err) else 0.0
