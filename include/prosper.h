@@ -73,9 +73,9 @@ extern "C" {
  *            4 (H D + H^2 + 8 (H D + 32 N_s + 3 H + 8 |K| + 64 + D)) bytes with
  *            N_s = 2 Hprime + Hprime (Hprime + 1)/2) within 227 KB; e.g.
  *            D = 64, H = 32, Hprime = 8, gamma = 3 uses 163 KB.
- * PROSPER_BF16_RESCORE (BSC only) additionally needs D % 64 == 0, H % 64 == 0 and
- * 2*H*D + 256*max(D, H) <= 226 KB (the BF16 dictionary and one operand tile
- * stay in shared memory), e.g. D = H = 256. */
+ * PROSPER_BF16_RESCORE (BSC only) additionally needs D % 64 == 0, D <= 256,
+ * H % 64 == 0 and 2 H D + 256 D + 28 KB <= 227 KB (the BF16 dictionary, one
+ * operand tile and the candidate buffers stay in shared memory), e.g. D = H = 256. */
 #define PROSPER_MAX_HPRIME 16
 #define PROSPER_MAX_STATES 4096
 
@@ -271,6 +271,21 @@ int prosper_serve_wait(prosper_ctx *ctx, uint64_t ticket, int timeout_ms,
                        int16_t *sel_host, float *s_mean_host, int16_t *map_idx_host,
                        float *map_p_host, float *logZ_host,
                        int64_t *t_submit_ns, int64_t *t_done_ns);
+
+/* Open-loop load generator for measuring the service (a measurement aid, not
+ * part of the method).  A submitter thread submits request i (sizes[i] points
+ * of the host pool Y_pool_host (pool_points x D), starting at row offsets[i])
+ * at arrival_ns[i] nanoseconds after the start, whatever happened to earlier
+ * requests; the calling thread polls every outstanding ticket without blocking
+ * and copies each finished request's outputs to host memory, as a client
+ * would.  Per request (host arrays of n_req): t_submit_ns (just before
+ * prosper_serve_submit), t_observed_ns (the client saw the results) and, if
+ * t_done_ns is not NULL, the scheduler's completion time; all CLOCK_MONOTONIC.
+ * Returns after every request finished, or with the first error. */
+int prosper_serve_loadgen(prosper_ctx *ctx, const float *Y_pool_host, int64_t pool_points,
+                          int n_req, const int32_t *sizes, const int64_t *offsets,
+                          const int64_t *arrival_ns, int64_t *t_submit_ns,
+                          int64_t *t_observed_ns, int64_t *t_done_ns);
 
 /* Stop the scheduler thread after the queued work finished; frees the slots. */
 int prosper_serve_stop(prosper_ctx *ctx);

@@ -41,6 +41,7 @@ ABI = {
     "prosper_serve_wait": (_I, [_P, ctypes.c_uint64, _I, _P, _P, _P, _P, _P,
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "prosper_serve_stop": (_I, [_P]),
+    "prosper_serve_loadgen": (_I, [_P, _P, _I64, _I, _P, _P, _P, _P, _P, _P]),
     "prosper_encode_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "prosper_status": (_I, [_P, _P]),
     "prosper_trace_enable": (_I, [_P, _I]),
@@ -272,6 +273,21 @@ class Context:
                "prosper_serve_wait")
         out["t_submit_ns"], out["t_done_ns"] = ts.value, td.value
         return out
+
+    def serve_loadgen(self, Y_pool: np.ndarray, sizes, offsets, arrival_s):
+        """Native open-loop load (prosper_serve_loadgen): request i of sizes[i]
+        rows of Y_pool from offsets[i], submitted arrival_s[i] seconds after the
+        start.  Returns per-request (t_submit, t_observed, t_done) in ns."""
+        Y_pool = np.ascontiguousarray(Y_pool, dtype=np.float32)
+        sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        arr = np.ascontiguousarray(np.round(np.asarray(arrival_s) * 1e9), dtype=np.int64)
+        n = len(sizes)
+        ts, to, td = (np.zeros(n, np.int64) for _ in range(3))
+        _check(self.lib.prosper_serve_loadgen(self.h, _ptr(Y_pool), int(Y_pool.shape[0]), n,
+                                              _ptr(sizes), _ptr(offsets), _ptr(arr), _ptr(ts),
+                                              _ptr(to), _ptr(td)), "prosper_serve_loadgen")
+        return ts, to, td
 
     def serve_stop(self):
         _check(self.lib.prosper_serve_stop(self.h), "prosper_serve_stop")

@@ -208,8 +208,9 @@ static int init_common(prosper_ctx **out, int model, int D, int H, int Hprime, i
         return PROSPER_EINVAL;
     }
     if (precision == PROSPER_BF16_RESCORE &&
-        (model != PROSPER_BSC || D % 64 != 0 || H % 64 != 0 || bf16_smem_bytes(D, H) > 227 * 1024)) {
-        set_error("BF16_RESCORE needs BSC, D %% 64 == 0, H %% 64 == 0 and 2HD + 256 max(D, H) <= 226 KB");
+        (model != PROSPER_BSC || D % 64 != 0 || H % 64 != 0 || D > 256 || bf16_smem_bytes(D, H) > 227 * 1024)) {
+        set_error("BF16_RESCORE needs BSC, D %% 64 == 0, D <= 256, H %% 64 == 0 and the BF16 dictionary, "
+                  "one operand tile and the candidate buffers within 227 KB of shared memory");
         return PROSPER_EINVAL;
     }
     if (max_points <= 0) max_points = 1 << 20;

@@ -97,6 +97,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // k-chunks of all tiles form one software pipeline: while chunk q is multiplied,
 // the Y values of chunk q+1 are in flight into registers and its W rows into the
 // other shared-memory stage (cp.async).
+// RMAX: the largest Hprime of the instantiation (10 or 16); the selection
+// rounds are unrolled up to it
+template <int RMAX>
 __global__ void __launch_bounds__(256, 1)
 k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
                const float *__restrict__ rnorm, int64_t N, int D, int H, int Hp, int score_mode,
@@ -271,7 +274,7 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
             int myh = 0x7fffffff;
             unsigned wlast = 0u, wnext = 0u;
 #pragma unroll
-            for (int r = 0; r <= PROSPER_MAX_HPRIME; ++r) {
+            for (int r = 0; r <= RMAX; ++r) {
                 if (r <= Hp) {   // warp-uniform
                     const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
                     if (lane == r && r < Hp) myh = 255 - (int)(w & 0xFFu);
@@ -296,7 +299,7 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
             }
             int rank = 0;
 #pragma unroll
-            for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
+            for (int r = 0; r < RMAX; ++r) {
                 const int o = __shfl_sync(0xffffffffu, myh, r);
                 rank += (r < Hp && o < myh) ? 1 : 0;
             }
@@ -836,13 +839,21 @@ int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
 int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s) {
     if (N <= 0) return PROSPER_OK;
     const size_t smem = sizeof(ProjSmem);
-    if (int rc = ensure_smem_attr((const void *)k_bsc_proj_f32, smem)) return rc;
+    const bool wide = c->Hp > BSC_REG_MAX_HPRIME;
+    const void *fn = wide ? (const void *)k_bsc_proj_f32<PROSPER_MAX_HPRIME>
+                          : (const void *)k_bsc_proj_f32<BSC_REG_MAX_HPRIME>;
+    if (int rc = ensure_smem_attr(fn, smem)) return rc;
     int64_t ntiles = (N + PT - 1) / PT;
     int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_f32", s);
-    k_bsc_proj_f32<<<grid, 256, smem, s>>>(Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->score_mode,
-                                           c->sel, c->selp, reinterpret_cast<float2 *>(c->yy),
-                                           c->d_status);
+    if (wide)
+        k_bsc_proj_f32<PROSPER_MAX_HPRIME><<<grid, 256, smem, s>>>(
+            Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->score_mode, c->sel, c->selp,
+            reinterpret_cast<float2 *>(c->yy), c->d_status);
+    else
+        k_bsc_proj_f32<BSC_REG_MAX_HPRIME><<<grid, 256, smem, s>>>(
+            Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->score_mode, c->sel, c->selp,
+            reinterpret_cast<float2 *>(c->yy), c->d_status);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }

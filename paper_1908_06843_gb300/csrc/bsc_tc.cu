@@ -33,13 +33,12 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;                       // points per tile (MMA M)
-constexpr int NW = 16;                        // warps per CTA
+constexpr int NSEL = 4;                       // selector warps (one per TMEM lane quadrant)
+constexpr int NLD = 4;                        // loader warps (Y -> BF16 operand, MMA issue)
+constexpr int NRS = 8;                        // rescore warps
+constexpr int NW = NSEL + NLD + NRS;          // 16 warps
+constexpr int CMAX = 32;                      // candidate slots per point (threshold pass)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded mbarrier wait: 2 s
-
-// index of float (row, col) in the swizzled projection stage (rows of H floats)
-__device__ __forceinline__ int pidx(int row, int col, int H) {
-    return row * H + ((((col >> 2) ^ (row & 7))) << 2) + (col & 3);
-}
 
 // byte offset of the 16-byte chunk c (8 BF16 values, d = 8c .. 8c+7) of row r in a
 // K-major 128-byte-swizzled operand with `rows` rows per 64-wide K-block
@@ -48,28 +47,70 @@ __device__ __forceinline__ uint32_t opnd_off(int r, int c, int rows) {
     return (uint32_t)(kb * rows * 128 + r * 128 + ((ch ^ (r & 7)) << 4));
 }
 
+// compare-exchange keeping the larger key first
+#define PROSPER_CX_DESC(a, b) { const unsigned _x = max(a, b), _y = min(a, b); a = _x; b = _y; }
+#define PROSPER_CX_ASC(a, b) { const int _x = min(a, b), _y = max(a, b); a = _x; b = _y; }
+
+// Batcher's odd-even merge sort of 16 values (63 comparators), by the given
+// compare-exchange
+#define PROSPER_SORT16(k, CX)                                                                 \
+    {                                                                                         \
+        _Pragma("unroll") for (int p_ = 1; p_ < 16; p_ <<= 1)                                 \
+        _Pragma("unroll") for (int q_ = p_; q_ > 0; q_ >>= 1)                                 \
+        _Pragma("unroll") for (int j_ = q_ % p_; j_ + q_ < 16; j_ += 2 * q_)                  \
+        _Pragma("unroll") for (int i_ = 0; i_ < q_; ++i_)                                     \
+            if (i_ + j_ + q_ < 16 && ((i_ + j_) / (2 * p_)) == ((i_ + j_ + q_) / (2 * p_)))          \
+                CX(k[i_ + j_], k[i_ + j_ + q_])                                                       \
+    }
+
+// Persistent, warp-specialised: per 128-point tile t (local index i),
+//   loader warps   Y tile -> BF16 operand (and exact y^T y), then one thread
+//                  issues the MMA chain into accumulator buffer i % 2 and commits
+//                  it to mma[i % 2];
+//   selector warps thread p = TMEM lane p = point p: the H scores of the point
+//                  straight from tensor memory, top-H' (see below), the chosen
+//                  latents ascending into sbuf[i % 2];
+//   rescore warps  one warp per point: the H' selected projections in FP32 from
+//                  the FP32 Y and W rows, written with the candidate lists.
+// Buffers are handed over with mbarriers (every wait bounded): mma[b] (MMA done:
+// accumulator readable and operand reusable), accfree[b] (selectors done with
+// accumulator b), selfull[b] / selfree[b] (candidate lists of buffer b written /
+// consumed).  The stages of consecutive tiles overlap.
+//
+// Top-H' of one point (R19: ranked on the score rounded down to 15 mantissa
+// bits, ties to the lower h, as a packed 32-bit key): pass 1 takes the maxima of
+// the H/16 groups of 16 scores; tau = the H'-th largest group maximum is a lower
+// bound of the H'-th largest score (H' distinct scores reach it), so only
+// scores whose rounded key reaches tau's can be chosen.  Pass 2 compacts those
+// candidates into per-thread shared slots; pass 3 inserts them into a sorted
+// register list.  With fewer groups than H', or more than CMAX candidates
+// (many equal scores), every score is inserted instead.
+template <int RB>
 __global__ void __launch_bounds__(NW * 32, 1)
 k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
-                const uint16_t *__restrict__ Wimg, const float *__restrict__ rnorm, int64_t N,
-                int D, int H, int Hp, uint32_t tmem_cols, int32_t *__restrict__ sel_out,
-                float *__restrict__ selp_out, float2 *__restrict__ yy_out,
-                unsigned *__restrict__ status, unsigned long long wait_ns, int test_no_commit) {
+                const uint16_t *__restrict__ Wimg, int64_t N, int D, int H, int Hp,
+                uint32_t tmem_cols, int32_t *__restrict__ sel_out, float *__restrict__ selp_out,
+                float2 *__restrict__ yy_out, unsigned *__restrict__ status,
+                unsigned long long wait_ns, int test_no_commit) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t bar_mma[2], bar_accfree[2], bar_selfull[2], bar_selfree[2];
     __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *sbase = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const size_t wbytes = (size_t)H * D * 2;
     unsigned char *Wsm = sbase;
     unsigned char *Ysm = sbase + ((wbytes + 1023) & ~(size_t)1023);
-    float *Psm = reinterpret_cast<float *>(Ysm);
+    int *sbuf = reinterpret_cast<int *>(Ysm + (size_t)TM * D * 2);          // 2 x TM x 16 latents
+    unsigned *cand = reinterpret_cast<unsigned *>(sbuf + 2 * TM * 16);       // CMAX x TM keys
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nchunk = D / 8;                 // 16-byte chunks per row
     const int nkb = D / 64;
     const int64_t ntiles = (N + TM - 1) / TM;
+    const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
     const uint32_t idesc = idesc_bf16(TM, H);
-    const uint32_t bar = smem_u32(&mbar);
+    const uint32_t HC = tmem_cols / 2;        // columns per accumulator buffer
 
     // resident BF16 dictionary (already in the operand image layout)
     {
@@ -78,7 +119,13 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
         for (size_t i = tid; i < wbytes / 16; i += NW * 32) dst[i] = __ldg(src + i);
     }
     if (tid == 0) {
-        mbar_init(bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bar_mma[b]), 1);
+            mbar_init(smem_u32(&bar_accfree[b]), NSEL);
+            mbar_init(smem_u32(&bar_selfull[b]), NSEL);
+            mbar_init(smem_u32(&bar_selfree[b]), NRS);
+        }
+        s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -92,261 +139,312 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    // per-lane key constants for h = lane + 32 j: the mask keeps the top 24 bits
-    // of the score key, the low byte holds 255 - h; both 0 for an absent latent
-    unsigned kmask[8], klow[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int h = lane + 32 * j;
-        kmask[j] = h < H ? 0xFFFFFF00u : 0u;
-        klow[j] = h < H ? (unsigned)(255 - h) : 0u;
-    }
+    // a wait that gave up: flag the status, stop every role of this CTA
+    auto wait_or_abort = [&](uint64_t *bar, uint32_t parity) {
+        if (s_abort) return false;
+        if (mbar_wait_sleep(smem_u32(bar), parity, wait_ns)) return true;
+        s_abort = 1;
+        atomicOr(status, ST_TC_TIMEOUT);
+        return false;
+    };
+    int issued = 0;   // MMA chains committed by this CTA (loader thread 0)
 
-    uint32_t phase = 0;
-    bool aborted = false;
-    for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
-        const int64_t n0 = tile * TM;
-        // ---- Y tile -> BF16 operand; exact y^T y on the way.  Warp w owns the
-        //      rows w + NW i (i < 8); all eight rows' loads are issued first.
-        float sq[TM / NW];
+    if (warp >= NSEL && warp < NSEL + NLD) {
+        // ------------------------------------------------------------ loaders
+        const int lw = warp - NSEL;
+        const uint64_t keep = policy_evict_last();   // the rescore reads these rows again
+        for (int i = 0; i < my_tiles; ++i) {
+            const int64_t n0 = (blockIdx.x + (int64_t)i * gridDim.x) * TM;
+            const int b = i & 1;
+            // the operand buffer is free once the previous tile's MMA completed;
+            // every loader takes the same decision (a bar.sync must not be left
+            // waiting for a warp that gave up)
+            const bool ok_op = i == 0 || wait_or_abort(&bar_mma[(i - 1) & 1], ((i - 1) >> 1) & 1);
+            if (named_sync_or(1, NLD * 32, !ok_op || s_abort)) break;
+            // warp lw converts rows lw + NLD r (r < TM / NLD); eight rows' loads in flight
+            for (int r0 = 0; r0 < TM / NLD; r0 += 8) {
+                float sq[8];
 #pragma unroll
-        for (int i = 0; i < TM / NW; ++i) sq[i] = 0.f;
-        for (int cb = 0; cb < nchunk; cb += 32) {
-            const int c = cb + lane;
-            float4 v0[TM / NW], v1[TM / NW];
+                for (int k = 0; k < 8; ++k) sq[k] = 0.f;
+                for (int cb = 0; cb < nchunk; cb += 32) {
+                    const int c = cb + lane;
+                    float4 v0[8], v1[8];
 #pragma unroll
-            for (int i = 0; i < TM / NW; ++i) {
-                const int64_t n = n0 + warp + NW * i;
-                v0[i] = v1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (c < nchunk && n < N) {
-                    const float4 *row = reinterpret_cast<const float4 *>(Y + n * D + 8 * c);
-                    v0[i] = __ldg(row);
-                    v1[i] = __ldg(row + 1);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < TM / NW; ++i) {
-                float q = sq[i];
-                q = fmaf(v0[i].x, v0[i].x, q); q = fmaf(v0[i].y, v0[i].y, q);
-                q = fmaf(v0[i].z, v0[i].z, q); q = fmaf(v0[i].w, v0[i].w, q);
-                q = fmaf(v1[i].x, v1[i].x, q); q = fmaf(v1[i].y, v1[i].y, q);
-                q = fmaf(v1[i].z, v1[i].z, q); q = fmaf(v1[i].w, v1[i].w, q);
-                sq[i] = q;
-                if (c < nchunk) {
-                    __nv_bfloat162 b0 = __floats2bfloat162_rn(v0[i].x, v0[i].y);
-                    __nv_bfloat162 b1 = __floats2bfloat162_rn(v0[i].z, v0[i].w);
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(v1[i].x, v1[i].y);
-                    __nv_bfloat162 b3 = __floats2bfloat162_rn(v1[i].z, v1[i].w);
-                    uint4 pk;
-                    pk.x = *reinterpret_cast<uint32_t *>(&b0);
-                    pk.y = *reinterpret_cast<uint32_t *>(&b1);
-                    pk.z = *reinterpret_cast<uint32_t *>(&b2);
-                    pk.w = *reinterpret_cast<uint32_t *>(&b3);
-                    *reinterpret_cast<uint4 *>(Ysm + opnd_off(warp + NW * i, c, TM)) = pk;
-                }
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < TM / NW; ++i) {
-            float q = sq[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-            const int64_t n = n0 + warp + NW * i;
-            if (lane == 0 && n < N) {
-                yy_out[n] = make_float2(q, 0.f);
-                if (!isfinite(q)) atomicOr(status, ST_NONFINITE);
-            }
-        }
-        fence_proxy_async();
-        __syncthreads();
-        // ---- projection tile on the tensor cores
-        if (tid == 0 && !test_no_commit) {
-            tc_fence_after();
-            const uint32_t ya = smem_u32(Ysm), wa = smem_u32(Wsm);
-            for (int kb = 0; kb < nkb; ++kb)
-#pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint64_t a = desc_sw128(ya + kb * TM * 128 + ks * 32);
-                    const uint64_t b = desc_sw128(wa + kb * H * 128 + ks * 32);
-                    umma_bf16(tmem, a, b, idesc, (kb | ks) != 0);
-                }
-            umma_commit(bar);
-        }
-        const bool ok = mbar_wait(bar, phase, wait_ns);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
-            aborted = true;
-            // give every point this CTA still owned a valid (if meaningless)
-            // candidate list so that later kernels stay in bounds
-            for (int64_t t2 = tile; t2 < ntiles; t2 += gridDim.x)
-                for (int i = tid; i < TM * SEL_STRIDE; i += NW * 32) {
-                    const int64_t nn = t2 * TM + i / SEL_STRIDE;
-                    if (nn >= N) continue;
-                    const int j = i % SEL_STRIDE;
-                    sel_out[nn * SEL_STRIDE + j] = j < H ? j : 0;
-                    selp_out[nn * SEL_STRIDE + j] = 0.f;
-                    if (j == 0) yy_out[nn] = make_float2(0.f, 0.f);
-                }
-            break;
-        }
-        tc_fence_after();
-
-        // ---- two halves of 64 points: TMEM -> shared P -> selection + FP32 rescore
-        for (int half = 0; half < 2; ++half) {
-            const int q = warp & 3;                 // TMEM lane quadrant of this warp
-            if ((q >> 1) == half) {
-                const int prow = (q & 1) * 32 + lane;   // row within the half
-                const int part = warp >> 2;             // 4 warps share a quadrant: H/4 columns each
-                const int cbeg = part * (H / 4);
-                const int cend = cbeg + H / 4;
-                for (int c0 = cbeg; c0 < cend; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-                    for (int k = 0; k < 16; k += 4)
-                        *reinterpret_cast<float4 *>(&Psm[pidx(prow, c0 + k, H)]) =
-                            make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-                }
-            }
-            tc_fence_before();
-            __syncthreads();
-            // packed keys: score key rounded down to 24 bits, then 255 - h, so that
-            // one 32-bit maximum ranks by score and breaks ties to the lower h
-            // (H <= 256); 0 marks an absent latent
-            auto make_keys = [&](int p, unsigned (&pk)[8]) {
-                const float *prow_p = Psm + pidx(p, lane, H);   // + 32 j for h = lane + 32 j
-#pragma unroll
-                for (int j = 0; j < 8; ++j) pk[j] = packed_key(kmask[j] ? prow_p[32 * j] : 0.f, kmask[j], klow[j]);
-                sort8_desc(pk);
-            };
-            auto rescore = [&](int64_t n, int myh) {
-                    // FP32 rescore: partial dot products over this lane's d, then a
-                    // transposed warp reduction (16 slots -> one total per lane pair)
-                    float v[16];
-#pragma unroll
-                    for (int r = 0; r < 16; ++r) v[r] = 0.f;
-                    const float *yrow = Y + n * D;
-                    int hsel[PROSPER_MAX_HPRIME];
-#pragma unroll
-                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r)
-                        hsel[r] = __shfl_sync(0xffffffffu, myh, r < Hp ? r : 0);
-                    for (int c = lane; c < nchunk; c += 32) {
-                        const float4 y0 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c));
-                        const float4 y1 = __ldg(reinterpret_cast<const float4 *>(yrow + 8 * c + 4));
-                        // rows in batches of 8: all of a batch's row loads first
-                        // (always in bounds), then its dot products
-#pragma unroll
-                        for (int rb = 0; rb < PROSPER_MAX_HPRIME; rb += 8) {
-                            if (rb >= Hp) break;   // warp-uniform
-                            float4 w[16];
-#pragma unroll
-                            for (int r = 0; r < 8; ++r) {
-                                const float *wrow = Wt + (size_t)hsel[rb + r] * D + 8 * c;
-                                w[2 * r] = __ldg(reinterpret_cast<const float4 *>(wrow));
-                                w[2 * r + 1] = __ldg(reinterpret_cast<const float4 *>(wrow + 4));
-                            }
-#pragma unroll
-                            for (int r = 0; r < 8; ++r) {
-                                const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
-                                float s = v[rb + r];
-                                s = fmaf(y0.x, w0.x, s); s = fmaf(y0.y, w0.y, s);
-                                s = fmaf(y0.z, w0.z, s); s = fmaf(y0.w, w0.w, s);
-                                s = fmaf(y1.x, w1.x, s); s = fmaf(y1.y, w1.y, s);
-                                s = fmaf(y1.z, w1.z, s); s = fmaf(y1.w, w1.w, s);
-                                v[rb + r] = (rb + r < Hp) ? s : 0.f;
-                            }
+                    for (int k = 0; k < 8; ++k) {
+                        const int64_t n = n0 + lw + NLD * (r0 + k);
+                        v0[k] = v1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (c < nchunk && n < N) {
+                            const float *row = Y + n * D + 8 * c;
+                            v0[k] = ldg_hint(row, keep);
+                            v1[k] = ldg_hint(row + 4, keep);
                         }
                     }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const bool up = (lane & 16) != 0;
-                        const float send = up ? v[k] : v[k + 8];
-                        const float keep = up ? v[k + 8] : v[k];
-                        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const bool up = (lane & 8) != 0;
-                        const float send = up ? v[k] : v[k + 4];
-                        const float keep = up ? v[k + 4] : v[k];
-                        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const bool up = (lane & 4) != 0;
-                        const float send = up ? v[k] : v[k + 2];
-                        const float keep = up ? v[k + 2] : v[k];
-                        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                    }
-                    {
-                        const bool up = (lane & 2) != 0;
-                        const float send = up ? v[0] : v[1];
-                        const float keep = up ? v[1] : v[0];
-                        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-                    }
-                    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-                    // this lane now holds the total of round index jr
-                    const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                                   ((lane >> 1) & 1);
-                    int rank = 0;
-#pragma unroll
-                    for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                        const int o = __shfl_sync(0xffffffffu, myh, r);
-                        rank += (r < Hp && o < myh) ? 1 : 0;
-                    }
-                    const int h_jr = __shfl_sync(0xffffffffu, myh, jr & 31);
-                    const int rank_jr = __shfl_sync(0xffffffffu, rank, jr & 31);
-                    if ((lane & 1) == 0 && jr < Hp) {
-                        sel_out[n * SEL_STRIDE + rank_jr] = h_jr;
-                        selp_out[n * SEL_STRIDE + rank_jr] = v[0];
-                    }
-                };
-            // two points at a time, so that the two selections' latency chains
-            // (warp maxima) interleave; then one rescore each
-            for (int i = 0; i < 64 / NW; i += 2) {
-                const int pa = warp * (64 / NW) + i, pb = pa + 1;
-                const int64_t na = n0 + 64 * half + pa, nb = na + 1;
-                if (na >= N) break;
-                unsigned ka[8], kb[8];
-                make_keys(pa, ka);
-                make_keys(pb, kb);
-                // Hp rounds of the warp maximum; the winning lane pops its head
-                int ha = 0, hb = 0;
-#pragma unroll
-                for (int r = 0; r < PROSPER_MAX_HPRIME; ++r) {
-                    if (r < Hp) {
-                        const unsigned wa = __reduce_max_sync(0xffffffffu, ka[0]);
-                        const unsigned wb = __reduce_max_sync(0xffffffffu, kb[0]);
-                        if (lane == r) {
-                            ha = 255 - (int)(wa & 0xFFu);
-                            hb = 255 - (int)(wb & 0xFFu);
-                        }
-                        if (ka[0] == wa) {
-#pragma unroll
-                            for (int j = 0; j < 7; ++j) ka[j] = ka[j + 1];
-                            ka[7] = 0u;
-                        }
-                        if (kb[0] == wb) {
-#pragma unroll
-                            for (int j = 0; j < 7; ++j) kb[j] = kb[j + 1];
-                            kb[7] = 0u;
+                        float q = sq[k];
+                        q = fmaf(v0[k].x, v0[k].x, q); q = fmaf(v0[k].y, v0[k].y, q);
+                        q = fmaf(v0[k].z, v0[k].z, q); q = fmaf(v0[k].w, v0[k].w, q);
+                        q = fmaf(v1[k].x, v1[k].x, q); q = fmaf(v1[k].y, v1[k].y, q);
+                        q = fmaf(v1[k].z, v1[k].z, q); q = fmaf(v1[k].w, v1[k].w, q);
+                        sq[k] = q;
+                        if (c < nchunk) {
+                            __nv_bfloat162 b0 = __floats2bfloat162_rn(v0[k].x, v0[k].y);
+                            __nv_bfloat162 b1 = __floats2bfloat162_rn(v0[k].z, v0[k].w);
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(v1[k].x, v1[k].y);
+                            __nv_bfloat162 b3 = __floats2bfloat162_rn(v1[k].z, v1[k].w);
+                            uint4 pk;
+                            pk.x = *reinterpret_cast<uint32_t *>(&b0);
+                            pk.y = *reinterpret_cast<uint32_t *>(&b1);
+                            pk.z = *reinterpret_cast<uint32_t *>(&b2);
+                            pk.w = *reinterpret_cast<uint32_t *>(&b3);
+                            *reinterpret_cast<uint4 *>(Ysm + opnd_off(lw + NLD * (r0 + k), c, TM)) = pk;
                         }
                     }
                 }
-                rescore(na, ha);
-                if (nb < N) rescore(nb, hb);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float q = sq[k];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+                    const int64_t n = n0 + lw + NLD * (r0 + k);
+                    if (lane == 0 && n < N) {
+                        yy_out[n] = make_float2(q, 0.f);
+                        if (!isfinite(q)) atomicOr(status, ST_NONFINITE);
+                    }
+                }
             }
-            __syncthreads();
+            fence_proxy_async();          // operand writes visible to the tensor cores
+            named_sync(1, NLD * 32);
+            if (lw == 0 && lane == 0) {
+                // accumulator b is free once the selectors finished tile i - 2
+                bool ok = i < 2 || wait_or_abort(&bar_accfree[b], ((i - 2) >> 1) & 1);
+                if (ok && !test_no_commit) {
+                    tc_fence_after();
+                    const uint32_t ya = smem_u32(Ysm), wa = smem_u32(Wsm);
+                    const uint32_t acc = tmem + (uint32_t)b * HC;
+                    for (int kb = 0; kb < nkb; ++kb)
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t a = desc_sw128(ya + kb * TM * 128 + ks * 32);
+                            const uint64_t bd = desc_sw128(wa + kb * H * 128 + ks * 32);
+                            umma_bf16(acc, a, bd, idesc, (kb | ks) != 0);
+                        }
+                    umma_commit(smem_u32(&bar_mma[b]));
+                    issued = i + 1;
+                }
+            }
+            if (named_sync_or(1, NLD * 32, s_abort != 0)) break;   // the same decision in every loader
+        }
+    } else if (warp < NSEL) {
+        // ---------------------------------------------------------- selectors
+        const int p = warp * 32 + lane;                       // point in the tile = TMEM lane
+        const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+        const int G = H / 16;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int b = i & 1;
+            // warp-uniform decisions: the TMEM loads below are .sync.aligned
+            if (!__all_sync(0xffffffffu, wait_or_abort(&bar_mma[b], (i >> 1) & 1))) break;
+            tc_fence_after();
+            const uint32_t acc = tmem + lane_addr + (uint32_t)b * HC;
+            unsigned top[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) top[s] = 0u;
+            auto insert = [&](unsigned key) {
+#pragma unroll
+                for (int s = 0; s < 16; ++s) PROSPER_CX_DESC(top[s], key);
+            };
+            bool full = Hp > G;
+            float thr = -INFINITY;
+            if (!full) {
+                // pass 1: group maxima, then tau = the Hp-th largest of them
+                float gm[16];
+#pragma unroll
+                for (int g = 0; g < 16; ++g) {
+                    gm[g] = -INFINITY;
+                    if (g < G) {
+                        float v[16];
+                        tmem_ld16_dep(acc + 16 * g, v);
+                        float m = v[0];
+#pragma unroll
+                        for (int j = 1; j < 16; ++j) m = fmaxf(m, v[j]);
+                        gm[g] = m;
+                    }
+                }
+                unsigned gk[16];
+#pragma unroll
+                for (int g = 0; g < 16; ++g) gk[g] = score_key(gm[g]);   // -inf -> smallest key
+                PROSPER_SORT16(gk, PROSPER_CX_DESC);
+                unsigned tk = gk[0];
+#pragma unroll
+                for (int s = 1; s < 16; ++s) tk = (s == Hp - 1) ? gk[s] : tk;
+                // the smallest float whose rounded key equals tau's rounded key:
+                // the key of x >= 0 is bits(x) | 2^31, of x < 0 it is ~bits(x)
+                const unsigned pre = tk & 0xFFFFFF00u;
+                const unsigned fb = (pre & 0x80000000u) ? (pre & 0x7FFFFFFFu) : ~pre;
+                thr = __uint_as_float(fb);
+                // pass 2: compact the candidates (rounded key >= tau's) into slots
+                int cnt = 0;
+#pragma unroll 1
+                for (int g = 0; g < G; ++g) {
+                    float v[16];
+                    tmem_ld16_dep(acc + 16 * g, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (v[j] >= thr) {
+                            if (cnt < CMAX) cand[cnt * TM + p] = packed_key(v[j], 0xFFFFFF00u, 255u - (16 * g + j));
+                            ++cnt;
+                        }
+                    }
+                }
+                // overflow in any lane sends the whole warp down the full path
+                // (its TMEM loads are .sync.aligned)
+                if (__any_sync(0xffffffffu, cnt > CMAX)) {
+                    full = true;
+                } else {
+                    // pass 3: sorted insertion of the candidates
+                    for (int c = 0; c < cnt; ++c) insert(cand[c * TM + p]);
+                }
+            }
+            if (full) {
+#pragma unroll 1
+                for (int g = 0; g < G; ++g) {
+                    float v[16];
+                    tmem_ld16_dep(acc + 16 * g, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) insert(packed_key(v[j], 0xFFFFFF00u, 255u - (16 * g + j)));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_accfree[b]));
+            // the chosen latents in ascending order (absent slots sort last)
+            int hs[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) hs[s] = (s < Hp) ? min(255 - (int)(top[s] & 0xFFu), H - 1) : 0x7fff;
+            PROSPER_SORT16(hs, PROSPER_CX_ASC);
+            if (!__all_sync(0xffffffffu, i < 2 || wait_or_abort(&bar_selfree[b], ((i - 2) >> 1) & 1))) break;
+            int4 *dst = reinterpret_cast<int4 *>(sbuf + (b * TM + p) * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_int4(hs[4 * q], hs[4 * q + 1], hs[4 * q + 2], hs[4 * q + 3]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_selfull[b]));
+        }
+    } else {
+        // ------------------------------------------------------------ rescore
+        // One warp per point, lane c holding the 8 values d = 8c .. 8c+7 (D <= 256).
+        // All of a point's rows (RB at a time: every row when Hprime <= 10) are
+        // requested before the first FMA, so each warp keeps up to 10 KB of
+        // gathers in flight.
+        const int rw = warp - NSEL - NLD;
+        const bool lane_on = lane < nchunk;
+        const uint64_t last_use = policy_evict_first();   // y: its last read
+        const uint64_t keep = policy_evict_last();        // W rows: read again and again
+        for (int i = 0; i < my_tiles; ++i) {
+            const int64_t n0 = (blockIdx.x + (int64_t)i * gridDim.x) * TM;
+            const int b = i & 1;
+            if (!__all_sync(0xffffffffu, wait_or_abort(&bar_selfull[b], (i >> 1) & 1))) break;
+            for (int p = rw; p < TM; p += NRS) {
+                const int64_t n = n0 + p;
+                if (n >= N) break;
+                const int *hsp = sbuf + (b * TM + p) * 16;
+                // lanes past D/8 load a valid chunk and use y = 0 (no contribution)
+                const int cl = lane_on ? lane : 0;
+                float4 y0 = ldg_hint(Y + n * D + 8 * cl, last_use);
+                float4 y1 = ldg_hint(Y + n * D + 8 * cl + 4, last_use);
+                if (!lane_on) y0 = y1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                float v[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[r] = 0.f;
+#pragma unroll
+                for (int rb = 0; rb < 16; rb += RB) {
+                    if (rb < Hp) {   // warp-uniform
+                        float4 w[2 * RB];
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) {
+                            if (rb + r < 16 && rb + r < Hp) {   // warp-uniform
+                                const float *wrow = Wt + (size_t)hsp[rb + r] * D + 8 * cl;
+                                w[2 * r] = ldg_hint(wrow, keep);
+                                w[2 * r + 1] = ldg_hint(wrow + 4, keep);
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < RB; ++r) {
+                            if (rb + r < 16 && rb + r < Hp) {
+                                const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
+                                float sacc = 0.f;
+                                sacc = fmaf(y0.x, w0.x, sacc); sacc = fmaf(y0.y, w0.y, sacc);
+                                sacc = fmaf(y0.z, w0.z, sacc); sacc = fmaf(y0.w, w0.w, sacc);
+                                sacc = fmaf(y1.x, w1.x, sacc); sacc = fmaf(y1.y, w1.y, sacc);
+                                sacc = fmaf(y1.z, w1.z, sacc); sacc = fmaf(y1.w, w1.w, sacc);
+                                v[rb + r] = sacc;
+                            }
+                        }
+                    }
+                }
+                // transposed warp reduction: 16 slots -> lane pair (2k, 2k+1) holds slot jr
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const bool up = (lane & 16) != 0;
+                    const float send = up ? v[q] : v[q + 8];
+                    const float keep = up ? v[q + 8] : v[q];
+                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool up = (lane & 8) != 0;
+                    const float send = up ? v[q] : v[q + 4];
+                    const float keep = up ? v[q + 4] : v[q];
+                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const bool up = (lane & 4) != 0;
+                    const float send = up ? v[q] : v[q + 2];
+                    const float keep = up ? v[q + 2] : v[q];
+                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+                {
+                    const bool up = (lane & 2) != 0;
+                    const float send = up ? v[0] : v[1];
+                    const float keep = up ? v[1] : v[0];
+                    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                }
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                               ((lane >> 1) & 1);
+                if ((lane & 1) == 0 && jr < Hp) {
+                    sel_out[n * SEL_STRIDE + jr] = hsp[jr];
+                    selp_out[n * SEL_STRIDE + jr] = v[0];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_selfree[b]));
         }
     }
-    if (aborted && tid == 0) {
-        // give the MMA chain that timed out one more bounded chance to finish
-        // before its tensor memory is released
-        mbar_wait(bar, phase ^ 1u, wait_ns / 2);
+
+    // ---------------------------------------------------------------- wind-down
+    if (s_abort && warp == NSEL && lane == 0 && issued > 0) {
+        // give the last MMA chain one more bounded chance to finish before its
+        // tensor memory is released
+        mbar_wait(smem_u32(&bar_mma[(issued - 1) & 1]), ((issued - 1) >> 1) & 1, wait_ns / 2);
     }
     tc_fence_before();
     __syncthreads();
+    if (s_abort) {
+        // give every point this CTA owned a valid (if meaningless) candidate
+        // list so that the later kernels stay in bounds
+        for (int t = 0; t < my_tiles; ++t) {
+            const int64_t t2 = blockIdx.x + (int64_t)t * gridDim.x;
+            for (int k = tid; k < TM * SEL_STRIDE; k += NW * 32) {
+                const int64_t nn = t2 * TM + k / SEL_STRIDE;
+                if (nn >= N) continue;
+                const int j = k % SEL_STRIDE;
+                sel_out[nn * SEL_STRIDE + j] = j < H ? j : 0;
+                selp_out[nn * SEL_STRIDE + j] = 0.f;
+                if (j == 0) yy_out[nn] = make_float2(0.f, 0.f);
+            }
+        }
+    }
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
@@ -375,8 +473,10 @@ __global__ void k_w_image(const float *__restrict__ Wt, const float *__restrict_
 
 size_t bf16_smem_bytes(int D, int H) {
     const size_t w = ((size_t)H * D * 2 + 1023) & ~(size_t)1023;
-    const size_t y = std::max((size_t)TM * D * 2, (size_t)64 * H * 4);
-    return 1024 + w + y;
+    const size_t y = (size_t)TM * D * 2;                       // BF16 operand of one tile
+    const size_t lists = 2 * (size_t)TM * 16 * 4;              // two buffers of candidate lists
+    const size_t cand = (size_t)CMAX * TM * 4;                 // selector candidate slots
+    return 1024 + w + y + lists + cand;
 }
 
 int launch_bsc_bf16_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
@@ -393,20 +493,28 @@ int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t
         return PROSPER_EINVAL;
     }
     const size_t smem = bf16_smem_bytes(c->D, c->H);
-    if (int rc = ensure_smem_attr((const void *)k_bsc_proj_bf16, smem)) return rc;
+    if (int rc = ensure_smem_attr((const void *)k_bsc_proj_bf16<10>, smem)) return rc;
+    if (int rc = ensure_smem_attr((const void *)k_bsc_proj_bf16<8>, smem)) return rc;
     uint32_t cols = 32;
     while ((int)cols < c->H) cols <<= 1;
+    cols *= 2;                          // two accumulator buffers
     const int64_t ntiles = (N + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_bf16", s);
     // fault-injection hook for the failure-detection test: the MMA chain is not
-    // issued, so the bounded wait runs out and the kernel reports a timeout
+    // issued, so the bounded waits run out and the kernel reports a timeout
     const unsigned long long wait_ns = c->tc_test_no_commit_ms > 0
                                            ? (unsigned long long)c->tc_test_no_commit_ms * 1000000ull
                                            : kWaitNs;
-    k_bsc_proj_bf16<<<grid, NW * 32, smem, s>>>(Y, W, c->Wb, c->rnorm, N, c->D, c->H, c->Hp, cols,
-                                            c->sel, c->selp, reinterpret_cast<float2 *>(c->yy),
-                                            c->d_status, wait_ns, c->tc_test_no_commit_ms > 0);
+    // rows gathered per batch in the rescore: all of them up to Hprime 10
+    if (c->Hp <= 10)
+        k_bsc_proj_bf16<10><<<grid, NW * 32, smem, s>>>(Y, W, c->Wb, N, c->D, c->H, c->Hp, cols, c->sel,
+                                                    c->selp, reinterpret_cast<float2 *>(c->yy), c->d_status,
+                                                    wait_ns, c->tc_test_no_commit_ms > 0);
+    else
+        k_bsc_proj_bf16<8><<<grid, NW * 32, smem, s>>>(Y, W, c->Wb, N, c->D, c->H, c->Hp, cols, c->sel,
+                                                   c->selp, reinterpret_cast<float2 *>(c->yy), c->d_status,
+                                                   wait_ns, c->tc_test_no_commit_ms > 0);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }

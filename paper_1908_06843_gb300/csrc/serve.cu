@@ -323,6 +323,78 @@ int prosper_serve_wait(prosper_ctx *c, uint64_t ticket, int timeout_ms, int16_t 
     return PROSPER_OK;
 }
 
+int prosper_serve_loadgen(prosper_ctx *c, const float *Y_pool_host, int64_t pool_points, int n_req,
+                          const int32_t *sizes, const int64_t *offsets, const int64_t *arrival_ns,
+                          int64_t *t_submit_ns, int64_t *t_observed_ns, int64_t *t_done_ns) {
+    if (!c || !c->serve) { set_error("serve_loadgen: service not started"); return PROSPER_ESTATE; }
+    if (!Y_pool_host || n_req < 0 || !sizes || !offsets || !arrival_ns || !t_submit_ns || !t_observed_ns) {
+        set_error("serve_loadgen: bad arguments");
+        return PROSPER_EINVAL;
+    }
+    for (int i = 0; i < n_req; ++i)
+        if (sizes[i] < 1 || sizes[i] > c->serve->slot_points || offsets[i] < 0 ||
+            offsets[i] + sizes[i] > pool_points) {
+            set_error("serve_loadgen: request %d (%d points at %lld) outside the pool or the slot size", i,
+                      sizes[i], (long long)offsets[i]);
+            return PROSPER_EINVAL;
+        }
+    const int D = c->D, Hp = c->Hp, g = c->gamma > 0 ? c->gamma : 1;
+    std::vector<uint64_t> tickets(n_req, 0);
+    std::vector<std::atomic<int>> state(n_req);   // 0 pending, 1 submitted, -1 submit failed
+    for (auto &x : state) x.store(0);
+    std::atomic<int> submit_rc{PROSPER_OK};
+    const int64_t t0 = now_ns() + 2000000;        // start 2 ms from now
+    // open-loop submitter: request i is submitted at t0 + arrival_ns[i] whatever
+    // the state of earlier requests (sleep until ~50 us before, then spin)
+    std::thread submitter([&] {
+        for (int i = 0; i < n_req; ++i) {
+            const int64_t due = t0 + arrival_ns[i];
+            for (;;) {
+                const int64_t left = due - now_ns();
+                if (left <= 0) break;
+                if (left > 60000) std::this_thread::sleep_for(std::chrono::nanoseconds(left - 50000));
+            }
+            t_submit_ns[i] = now_ns();
+            const int rc = prosper_serve_submit(c, Y_pool_host + offsets[i] * D, sizes[i], &tickets[i]);
+            if (rc) { submit_rc.store(rc); state[i].store(-1); break; }
+            state[i].store(1, std::memory_order_release);
+        }
+    });
+    // observer: polls every outstanding ticket without blocking and copies each
+    // finished request's results to host memory, as a client would
+    std::vector<int16_t> o_sel((size_t)c->serve->slot_points * Hp), o_map((size_t)c->serve->slot_points * g);
+    std::vector<float> o_sm((size_t)c->serve->slot_points * Hp), o_p(c->serve->slot_points), o_z(c->serve->slot_points);
+    int rc = PROSPER_OK, next = 0, remaining = n_req;
+    std::vector<int> open;
+    while (remaining > 0 && !rc) {
+        while (next < n_req && state[next].load(std::memory_order_acquire) != 0) {
+            if (state[next].load() < 0) { rc = submit_rc.load(); break; }
+            open.push_back(next++);
+        }
+        if (rc) break;
+        bool any = false;
+        for (size_t k = 0; k < open.size();) {
+            const int i = open[k];
+            int64_t td = 0;
+            const int w = prosper_serve_wait(c, tickets[i], 0, o_sel.data(), o_sm.data(), o_map.data(),
+                                             o_p.data(), o_z.data(), nullptr, &td);
+            if (w == PROSPER_ETIMEOUT) { ++k; continue; }
+            if (w) { rc = w; break; }
+            t_observed_ns[i] = now_ns();
+            if (t_done_ns) t_done_ns[i] = td;
+            open[k] = open.back();
+            open.pop_back();
+            --remaining;
+            any = true;
+        }
+        if (!any) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    }
+    submitter.join();
+    if (rc) return rc;
+    set_error("%s", "");
+    return PROSPER_OK;
+}
+
 int prosper_serve_stop(prosper_ctx *c) {
     if (!c || !c->serve) return PROSPER_OK;
     ServeState *S = c->serve;

@@ -32,6 +32,40 @@ static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, 
         if (gtime_ns() - t0 > limit_ns) return false;
     }
 }
+// The same bounded wait with mbarrier.try_wait: the thread may be suspended
+// (up to a 100 us hint, or until the phase completes) instead of spinning, so
+// waiting warps leave the issue slots to the working ones.
+static __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
+                                                       unsigned long long limit_ns) {
+    const unsigned long long t0 = gtime_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(bar), "r"(parity), "r"(100000u) : "memory");
+        if (done) return true;
+        if (gtime_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// L2 eviction-priority policies and 16-byte global loads that carry them
+static __device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+static __device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+static __device__ __forceinline__ float4 ldg_hint(const float *ptr, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(ptr), "l"(pol));
+    return v;
+}
 // One arrival that also announces `bytes` of asynchronous transfers to come.
 static __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
@@ -95,6 +129,44 @@ static __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane, with the wait for
+// the load folded in as a register dependency (the values cannot be used
+// before tcgen05.wait::ld has retired the load)
+static __device__ __forceinline__ void tmem_ld16_dep(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// one plain arrival on an mbarrier (release semantics at CTA scope)
+static __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+// barrier over a subset of the CTA's warps (named barrier id, thread count)
+static __device__ __forceinline__ void named_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+// the same barrier, returning the OR of a predicate over its threads
+static __device__ __forceinline__ bool named_sync_or(int id, int threads, bool pred) {
+    unsigned r;
+    asm volatile("{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n"
+                 " bar.red.or.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+                 : "=r"(r) : "r"((unsigned)pred), "r"(id), "r"(threads) : "memory");
+    return r != 0;
+}
 
 }  // namespace tc
 }  // namespace prosper
