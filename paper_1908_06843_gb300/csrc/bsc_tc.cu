@@ -347,11 +347,12 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 const int64_t n = n0 + p;
                 if (n >= N) break;
                 const int *hsp = sbuf + (b * TM + p) * 16;
-                // lanes past D/8 load a valid chunk and use y = 0 (no contribution)
-                const int cl = lane_on ? lane : 0;
-                float4 y0 = ldg_hint(Y + n * D + 8 * cl, last_use);
-                float4 y1 = ldg_hint(Y + n * D + 8 * cl + 4, last_use);
-                if (!lane_on) y0 = y1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
+                if (lane_on) {
+                    const float *yrow = Y + n * D + 8 * lane;
+                    y0 = ldg_hint(yrow, last_use);
+                    y1 = ldg_hint(yrow + 4, last_use);
+                }
                 float v[16];
 #pragma unroll
                 for (int r = 0; r < 16; ++r) v[r] = 0.f;
@@ -361,15 +362,16 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                         float4 w[2 * RB];
 #pragma unroll
                         for (int r = 0; r < RB; ++r) {
-                            if (rb + r < 16 && rb + r < Hp) {   // warp-uniform
-                                const float *wrow = Wt + (size_t)hsp[rb + r] * D + 8 * cl;
+                            w[2 * r] = w[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (rb + r < 16 && rb + r < Hp && lane_on) {
+                                const float *wrow = Wt + (size_t)hsp[rb + r] * D + 8 * lane;
                                 w[2 * r] = ldg_hint(wrow, keep);
                                 w[2 * r + 1] = ldg_hint(wrow + 4, keep);
                             }
                         }
 #pragma unroll
                         for (int r = 0; r < RB; ++r) {
-                            if (rb + r < 16 && rb + r < Hp) {
+                            if (rb + r < 16) {
                                 const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
                                 float sacc = 0.f;
                                 sacc = fmaf(y0.x, w0.x, sacc); sacc = fmaf(y0.y, w0.y, sacc);
