@@ -30,7 +30,7 @@ _OUT = os.path.join(_HERE, "_build", "libprosper_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BSC, MCA, GSC, TSC, DSC = 0, 1, 2, 3, 4
+BSC, MCA, GSC, TSC, DSC, MMCA = 0, 1, 2, 3, 4, 5
 SC_F, SC_S1, SC_YY, SC_N, SC_MCA_R2, SC_DSC0, SC_LEN = 0, 1, 2, 3, 4, 5, 8
 TH_LEN = 12
 TSC_VALUES = (-1.0, 1.0)
@@ -146,7 +146,7 @@ def estep(model, Y, Wt, pi, sigma, Hp, gamma, rho=0.0, mu=None, psi=None,
         logZ=np.zeros(N), At=np.zeros((H, D)), B=np.zeros((H, H)),
         scal=np.zeros(SC_LEN),
         gsc=np.zeros(3 * H) if model == GSC else None,
-        mca=np.zeros(2 * H * D) if model == MCA else None,
+        mca=np.zeros(2 * H * D) if model in (MCA, MMCA) else None,
     )
     rc = lib.orc_estep(model, N, D, H, Hp, gamma, _p(Y), _p(Wt), _p(th), _p(mu), _p(psi),
                        _p(si), _p(out["sel"]), _p(out["smean"]),

@@ -10,7 +10,9 @@
  * What it computes (paper: Exarchakis et al., "ProSper", JMLR MLOSS):
  *   - The generative model template of Eq. 1-2: a prior p(s|Theta) and a
  *     noise model p(y|s,Theta) = p(y; f(Theta,s)), with the per-model prior,
- *     noise and superposition f from Table 1 (rows BSC, TSC, DSC, GSC, MCA).
+ *     noise and superposition f from Table 1 (rows BSC, TSC, DSC, GSC, MCA,
+ *     MMCA).  MMCA is MCA with a signed dictionary whose superposition takes,
+ *     per pixel, the active component of largest magnitude.
  *     TSC and DSC are linear superpositions like BSC with latents taking
  *     values in a finite set Phi = {0, phi_1, .., phi_m} under a categorical
  *     prior (TSC: Phi = {-1, 0, 1}, zero-mean: p(-1) = p(1) = pi/2).
@@ -42,7 +44,7 @@
 #include <omp.h>
 #endif
 
-enum { ORC_BSC = 0, ORC_MCA = 1, ORC_GSC = 2, ORC_TSC = 3, ORC_DSC = 4 };
+enum { ORC_BSC = 0, ORC_MCA = 1, ORC_GSC = 2, ORC_TSC = 3, ORC_DSC = 4, ORC_MMCA = 5 };
 
 /* scal[] layout of the aggregated scalar statistics; SC_DSC0 + v holds
  * sum_n sum_h <[s_h = phi_{v+1}]> (TSC/DSC: expected count of each nonzero value) */
@@ -220,7 +222,7 @@ static void scratch_alloc(scratch_t *s, const problem_t *p) {
     s->CW = p->model == ORC_GSC ? malloc(sizeof(double) * D * g) : NULL;
     s->kappa = malloc(sizeof(double) * p->nK * p->Hp);
     s->lambda = malloc(sizeof(double) * p->nK * p->Hp * p->Hp);
-    s->Abar = p->model == ORC_MCA ? malloc(sizeof(double) * p->Hp * D) : NULL;
+    s->Abar = (p->model == ORC_MCA || p->model == ORC_MMCA) ? malloc(sizeof(double) * p->Hp * D) : NULL;
 }
 
 static void scratch_free(scratch_t *s) {
@@ -244,6 +246,22 @@ static double log_prior_dsc(const problem_t *p, uint32_t mask, uint32_t vcode) {
 }
 
 static int is_discrete(const problem_t *p) { return p->model == ORC_TSC || p->model == ORC_DSC; }
+static int is_maxlike(const problem_t *p) { return p->model == ORC_MCA || p->model == ORC_MMCA; }
+
+/* Superposition of the max models at one pixel over the active units gidx[0..k)
+ * (Table 1): MCA f_d = max_h W_dh s_h (W >= 0); MMCA f_d = the W_dh of largest
+ * |W_dh| among the active units (the first in unit order on a tie in |W|).
+ * 0 for the empty state. */
+static double superpose_max(const problem_t *p, const int *gidx, int k, int d) {
+    double f = 0.0;
+    for (int i = 0; i < k; ++i) {
+        double w = p->Wt[(size_t)gidx[i] * p->D + d];
+        if (i == 0) f = w;
+        else if (p->model == ORC_MMCA) f = fabs(w) > fabs(f) ? w : f;
+        else f = w > f ? w : f;
+    }
+    return f;
+}
 
 /* Gaussian log-density N(y; m, v I_D) with v = sigma^2, from ||y - m||^2. */
 static double log_gauss_iso(int D, double sigma, double r2) {
@@ -339,9 +357,11 @@ static void selection_scores(const problem_t *p, scratch_t *s, const double *y) 
                 sc = (pos && neg) ? fabs(sc) : (neg ? -sc : sc);
             }
             s->score[h] = sc;
-        } else if (p->model == ORC_MCA) {
+        } else if (is_maxlike(p)) {
+            /* MCA: sum_d W_dh y_d / sum_d W_dh; MMCA (reading, W signed):
+             * sum_d W_dh y_d / sum_d |W_dh| */
             double pr = 0.0, sw = 0.0;
-            for (int d = 0; d < D; ++d) { pr += w[d] * y[d]; sw += w[d]; }
+            for (int d = 0; d < D; ++d) { pr += w[d] * y[d]; sw += p->model == ORC_MMCA ? fabs(w[d]) : w[d]; }
             s->score[h] = sw > 0.0 ? pr / sw : 0.0;
         } else {
             int g = h;
@@ -391,14 +411,13 @@ static double log_joint(const problem_t *p, scratch_t *s, const double *y,
         }
         return log_prior_dsc(p, mask, vcode) + log_gauss_iso(D, p->sigma, r2);
     }
-    /* f(Theta, s): BSC linear superposition W s; MCA max_h W_dh s_h (0 if s=0) */
+    /* f(Theta, s): BSC linear superposition W s; MCA / MMCA the (magnitude) max */
     for (int d = 0; d < D; ++d) {
         double f = 0.0;
-        for (int i = 0; i < k; ++i) {
-            double w = p->Wt[(size_t)gidx[i] * D + d];
-            if (p->model == ORC_BSC) f += w;
-            else f = (i == 0) ? w : (w > f ? w : f);
-        }
+        if (p->model == ORC_BSC)
+            for (int i = 0; i < k; ++i) f += p->Wt[(size_t)gidx[i] * D + d];
+        else
+            f = superpose_max(p, gidx, k, d);
         s->f[d] = f;
     }
     double r2 = 0.0;
@@ -499,10 +518,11 @@ static void point_estep(const problem_t *p, scratch_t *s, const double *y,
             }
         }
     }
-    if (p->model == ORC_MCA) {
+    if (is_maxlike(p)) {
         /* <||y - f(s)||^2> with the hard max (sigma update, reading R8) and
-         * <A_dh> with A_dh(s) = s_h (W_dh / Wbar_d(s))^(rho-1),
-         * Wbar_d(s) = (sum_{h in s} W_dh^rho)^(1/rho)  (rho-smoothed max). */
+         * <A_dh> with A_dh(s) = s_h (|W_dh| / Wbar_d(s))^(rho-1),
+         * Wbar_d(s) = (sum_{h in s} |W_dh|^rho)^(1/rho)  (rho-smoothed max of
+         * the magnitudes; |W| = W for MCA). */
         memset(s->Abar, 0, sizeof(double) * Hp * D);
         for (int kk = 0; kk < nK; ++kk) {
             uint32_t mask = p->K[kk];
@@ -511,24 +531,21 @@ static void point_estep(const problem_t *p, scratch_t *s, const double *y,
             for (int j = 0; j < Hp; ++j) if (mask & (1u << j)) { loc[k] = j; gidx[k++] = o->sel[j]; }
             double r2 = 0.0;
             for (int d = 0; d < D; ++d) {
-                double f = 0.0;
-                for (int i = 0; i < k; ++i) {
-                    double w = p->Wt[(size_t)gidx[i] * D + d];
-                    f = (i == 0) ? w : (w > f ? w : f);
-                }
+                double f = superpose_max(p, gidx, k, d);
                 r2 += (y[d] - f) * (y[d] - f);
                 if (k == 0) continue;
-                /* Wbar = m (sum (W/m)^rho)^(1/rho) with m = max: the same
-                 * value, without overflow of W^rho for large rho */
+                /* Wbar = m (sum (|W|/m)^rho)^(1/rho) with m = max |W|: the same
+                 * value, without overflow of |W|^rho for large rho */
                 double mx = 0.0, sp = 0.0;
                 for (int i = 0; i < k; ++i) {
-                    double w = p->Wt[(size_t)gidx[i] * D + d];
+                    double w = fabs(p->Wt[(size_t)gidx[i] * D + d]);
                     mx = w > mx ? w : mx;
                 }
-                for (int i = 0; i < k; ++i) sp += pow(p->Wt[(size_t)gidx[i] * D + d] / mx, p->rho);
+                if (!(mx > 0.0)) continue;          /* every active |W_dh| is 0: no factor */
+                for (int i = 0; i < k; ++i) sp += pow(fabs(p->Wt[(size_t)gidx[i] * D + d]) / mx, p->rho);
                 double wbar = mx * pow(sp, 1.0 / p->rho);
                 for (int i = 0; i < k; ++i) {
-                    double w = p->Wt[(size_t)gidx[i] * D + d];
+                    double w = fabs(p->Wt[(size_t)gidx[i] * D + d]);
                     s->Abar[loc[i] * D + d] += q * pow(w / wbar, p->rho - 1.0);
                 }
             }
@@ -757,13 +774,14 @@ int orc_mstep(int model, int D, int H, double Ntot, const double *At,
               const double *B, const double *scal, const double *gsc,
               const double *mca, double *Wt, double *theta, double *mu,
               double *psi) {
-    if (model == ORC_MCA) {
+    if (model == ORC_MCA || model == ORC_MMCA) {
+        /* MCA keeps W >= 1e-6 (its powers need W > 0); MMCA's W is signed */
         for (int h = 0; h < H; ++h)
             for (int d = 0; d < D; ++d) {
                 double num = mca[(size_t)h * D + d], den = mca[(size_t)H * D + (size_t)h * D + d];
                 if (den > 0.0) {
                     double w = num / den;
-                    Wt[(size_t)h * D + d] = w < 1e-6 ? 1e-6 : w;
+                    Wt[(size_t)h * D + d] = (model == ORC_MCA && w < 1e-6) ? 1e-6 : w;
                 }
             }
         theta[0] = scal[SC_S1] / (Ntot * H);

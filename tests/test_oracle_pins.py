@@ -447,6 +447,123 @@ def test_mca_selection_known_answer(orc):
 
 
 # ---------------------------------------------------------------------------
+# MMCA (Table 1: |max| superposition, signed dictionary, binary latents)
+# ---------------------------------------------------------------------------
+def brute_logjoint_mmca(y, Wt, pi, sigma):
+    """log p(s, y) over {0,1}^H: per pixel the active W_dh of largest |W_dh|
+    (first in unit order on a tie), scipy's Gaussian density."""
+    H, D = Wt.shape
+    S = all_states(H)
+    k = S.sum(1)
+    lp = k * np.log(pi) + (H - k) * np.log(1 - pi)
+    F = np.zeros((len(S), D))
+    for i, s_ in enumerate(S):
+        act = np.flatnonzero(s_)
+        if len(act):
+            win = act[np.argmax(np.abs(Wt[act]), axis=0)]      # argmax takes the first on ties
+            F[i] = Wt[win, np.arange(D)]
+    ll = multivariate_normal(mean=np.zeros(D), cov=sigma ** 2 * np.eye(D)).logpdf(y[None, :] - F)
+    return S, lp + ll
+
+
+def _small_mmca(seed, H=6, D=7, N=3):
+    g = synth.rng(seed)
+    Wt = g.standard_normal((H, D)) * 2.0
+    S = (g.random((N, H)) < 0.3).astype(float)
+    Y = np.zeros((N, D))
+    for n in range(N):
+        act = np.flatnonzero(S[n])
+        if len(act):
+            win = act[np.argmax(np.abs(Wt[act]), axis=0)]
+            Y[n] = Wt[win, np.arange(D)]
+    return Y + g.standard_normal((N, D)), Wt
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_mmca_exact_equals_bruteforce(orc, seed):
+    Y, Wt = _small_mmca(seed)
+    H = Wt.shape[0]
+    for y in Y:
+        post = orc.posterior(orc.MMCA, y, Wt, 0.3, 0.9, H, H, rho=20)
+        S, lj = brute_logjoint_mmca(y, Wt, 0.3, 0.9)
+        idx = match_states(state_vectors(post, H), S)
+        np.testing.assert_allclose(post["ell"], lj[idx], rtol=1e-12, atol=1e-10)
+        np.testing.assert_allclose(post["q"], np.exp(lj - logsumexp(lj))[idx], rtol=1e-10, atol=1e-14)
+
+
+def test_mmca_nonnegative_dictionary_is_mca(orc):
+    """With W > 0 the largest magnitude is the largest value: MMCA = MCA in the
+    E-step and its rho-smoothed statistics; the M-steps agree wherever MCA's
+    positivity clamp (W >= 1e-6) is not active, and where it is, MMCA keeps
+    the unclamped (signed) update."""
+    Y, Wt = _small_mca(7, N=12)
+    Wt = Wt + 0.5
+    a = orc.estep(orc.MMCA, Y, Wt, 0.2, 1.1, 4, 2, rho=20)
+    b = orc.estep(orc.MCA, Y, Wt, 0.2, 1.1, 4, 2, rho=20)
+    for k in ("sel", "smean", "logZ", "mca", "scal"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-13)
+    Wa = orc.mstep(orc.MMCA, 12, a, Wt, 0.2, 1.1)[0]
+    Wb = orc.mstep(orc.MCA, 12, b, Wt, 0.2, 1.1)[0]
+    free = Wb > 1e-6
+    np.testing.assert_allclose(Wa[free], Wb[free], rtol=1e-12)
+    assert np.all(Wa[~free] <= 1e-6)
+
+
+def test_mmca_gamma1_equals_bsc_gamma1(orc):
+    """At most one active unit: f = W_h s_h, the linear superposition."""
+    Y, Wt = _small_mmca(3, N=10)
+    sel = np.tile(np.array([0, 2, 3, 5], np.int32), (len(Y), 1))
+    a = orc.estep(orc.MMCA, Y, Wt, 0.2, 1.1, 4, 1, rho=20, sel_in=sel)
+    b = orc.estep(orc.BSC, Y, Wt, 0.2, 1.1, 4, 1, sel_in=sel)
+    np.testing.assert_allclose(a["smean"], b["smean"], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(a["logZ"], b["logZ"], rtol=1e-12)
+
+
+def test_mmca_mstep_limits(orc):
+    """gamma = 1: A_dh = s_h, W_dh = sum<s_h> y_d / sum<s_h> (signs kept, no
+    clamp); rho -> infinity: the unit of largest |W_dh| takes pixel d."""
+    Y, Wt = _small_mmca(4, N=30)
+    H, D = Wt.shape
+    out = orc.estep(orc.MMCA, Y, Wt, 0.2, 1.1, H, 1, rho=20)
+    num = np.zeros((H, D))
+    den = np.zeros(H)
+    for y in Y:
+        post = orc.posterior(orc.MMCA, y, Wt, 0.2, 1.1, H, 1, rho=20)
+        for q, v in zip(post["q"], state_vectors(post, H)):
+            num += q * v[:, None] * y[None, :]
+            den += q * v
+    W2 = orc.mstep(orc.MMCA, len(Y), out, Wt, 0.2, 1.1)[0]
+    np.testing.assert_allclose(W2, num / den[:, None], rtol=1e-10)
+    assert np.any(W2 < 0)
+    rho = 3000.0
+    out = orc.estep(orc.MMCA, Y, Wt, 0.3, 1.0, H, 3, rho=rho)
+    num = np.zeros((H, D))
+    den = np.zeros((H, D))
+    for y in Y:
+        post = orc.posterior(orc.MMCA, y, Wt, 0.3, 1.0, H, 3, rho=rho)
+        for q, v in zip(post["q"], state_vectors(post, H)):
+            act = np.flatnonzero(v)
+            if not len(act):
+                continue
+            win = act[np.argmax(np.abs(Wt[act]), axis=0)]
+            for d in range(D):
+                num[win[d], d] += q * y[d]
+                den[win[d], d] += q
+    W2 = orc.mstep(orc.MMCA, len(Y), out, Wt, 0.3, 1.0)[0]
+    m = den > 1e-3
+    np.testing.assert_allclose(W2[m], num[m] / den[m], rtol=2e-3, atol=1e-3)
+
+
+def test_mmca_selection_uses_magnitude_normaliser(orc):
+    """MMCA score (reading): sum_d W_dh y_d / sum_d |W_dh|, worked by hand."""
+    Wt = np.array([[1.0, -1.0, 0.0], [2.0, 0.0, 2.0], [0.0, -3.0, 1.0]])
+    y = np.array([2.0, -1.0, 4.0])
+    # h0: (2 + 1) / 2 = 1.5; h1: (4 + 8) / 4 = 3; h2: (3 + 4) / 4 = 1.75
+    np.testing.assert_array_equal(orc.scores(orc.MMCA, y, Wt), [1.5, 3.0, 1.75])
+    assert orc.posterior(orc.MMCA, y, Wt, 0.2, 1.0, 2, 1, rho=20)["sel"].tolist() == [1, 2]
+
+
+# ---------------------------------------------------------------------------
 # TSC / DSC (Table 1: linear superposition, discrete latents, categorical prior)
 # ---------------------------------------------------------------------------
 DSC_VALS = np.array([0.5, 2.0, -1.5])
