@@ -400,22 +400,28 @@ def serve_sweep(torch, Y, Wt, rates=(1e3, 4e3, 1.6e4, 3.2e4, 6.4e4, 1.28e5, 2.56
 
 
 def secondary_configs(torch, dev, steps, warmup):
-    """E-step (and M-step) throughput of the other two model rows on their own
-    workloads: MCA max-superposition bars (D=100, H=20, H'=8, gamma=4, 163 states,
-    N=100,000) and GSC spike-and-slab (D=64, H=32, H'=8, gamma=3, 93 states,
-    N=50,000), at the generating parameters (MCA W shifted by 0.05 > 0)."""
-    from paper_1908_06843_gb300 import FP32, GSC, MCA, Context, synth
+    """E-step throughput of the other model rows on their own workloads: MCA
+    max-superposition bars (D=100, H=20, H'=8, gamma=4, 163 states, N=100,000),
+    MMCA on the same bars with random signs, TSC on Gabor-dictionary data
+    (D=256, H=64, H'=8, gamma=3, 577 ternary states, N=100,000) and GSC
+    spike-and-slab (D=64, H=32, H'=8, gamma=3, 93 states, N=50,000), at the
+    generating parameters (MCA W shifted by 0.05 > 0)."""
+    from paper_1908_06843_gb300 import FP32, GSC, MCA, MMCA, TSC, Context, synth
     out = {}
     cases = [
         ("mca_bars", MCA, synth.mca_bars(N=100_000, seed=1003), 8, 4, 0.1, 1.0, 20.0,
          "MCA bars D=100 H=20 H'=8 gamma=4 (163 states) N=100000, FP32"),
+        ("mmca_signed_bars", MMCA, synth.mmca_bars(N=100_000, seed=1005), 8, 4, 0.1, 1.0, 20.0,
+         "MMCA signed bars D=100 H=20 H'=8 gamma=4 (163 states) N=100000, FP32"),
+        ("tsc_gabor", TSC, synth.discrete(N=100_000, seed=1006), 8, 3, 4.0 / 64.0, 0.2, 0.0,
+         "TSC Gabor D=256 H=64 H'=8 gamma=3 (577 states) N=100000, FP32"),
         ("gsc", GSC, synth.gsc(N=50_000, seed=1004), 8, 3, 3.0 / 32.0, 0.3, 0.0,
          "GSC D=64 H=32 H'=8 gamma=3 (93 states) N=50000, FP32 states + FP64 subset table"),
     ]
     for name, model, d, hp, gamma, pi, sigma, rho, label in cases:
         try:
             Y = np.asarray(d["Y"], np.float32)
-            Wt = np.asarray(d["Wt"] + (0.05 if model == MCA else 0.0), np.float32)
+            Wt = np.asarray(d["Wt"] + (0.05 if model == MCA else 0.0), np.float32)   # MCA: W > 0
             n, dd = Y.shape
             hh = Wt.shape[0]
             ctx = Context(model, dd, hh, hp, gamma, FP32, max_points=n)

@@ -54,6 +54,8 @@ extern "C" {
                           prior p(s_h = -1) = p(s_h = 1) = pi/2 */
 #define PROSPER_DSC 4  /* discrete sparse coding: linear f = W s, s_h in {0, phi_1 .. phi_m} (m <= 3 values
                           fixed by prosper_init_dsc), categorical prior p(s_h = phi_v) = theta[TH_DSC_P + v] */
+#define PROSPER_MMCA 5 /* max-magnitude causes: f_d = W_dh* with h* the active unit of largest |W_dh|
+                          (the lower h on a tie), signed W, binary latents, Bernoulli(pi) prior */
 
 /* Precision of the BSC preselection projection W^T y (other models: FP32 only). */
 #define PROSPER_FP32          0  /* FP32 SIMT projection; exact top-H' of the FP32 scores */
@@ -67,7 +69,7 @@ extern "C" {
  *   BSC:     1 <= Hprime <= 16, |K| <= 4096 states per point; for Hprime > 10 also
  *            gamma <= 8 (those use the table-driven state kernel).
  *   TSC/DSC: 1 <= Hprime <= 16, gamma <= 8, |K| = sum_{k<=gamma} C(Hprime,k) m^k <= 4096.
- *   MCA:     1 <= Hprime <= 16, |K| <= 1024, D <= 256.
+ *   MCA/MMCA: 1 <= Hprime <= 16, |K| <= 1024, D <= 256.
  *   GSC:     1 <= Hprime <= 10, gamma <= 3, H <= 32, D <= 256, and the E-step's
  *            shared memory (dictionary, Gram matrix, per-warp slots, about
  *            4 (H D + H^2 + 8 (H D + 32 N_s + 3 H + 8 |K| + 64 + D)) bytes with
@@ -120,7 +122,7 @@ typedef struct {
     double *B;     /* H x H: sum_n <s s^T>_n (full symmetric matrix)                  */
     double *scal;  /* PROSPER_SC_LEN scalars (layout above)                            */
     double *gsc;   /* GSC: 3H = [sum <b_h>, sum <s_h>, sum <s_h^2>]; NULL otherwise     */
-    double *mca;   /* MCA: 2 H D = [sum <A_dh> y_dn (H x D), sum <A_dh> (H x D)]; else NULL */
+    double *mca;   /* MCA/MMCA: 2 H D = [sum <A_dh> y_dn (H x D), sum <A_dh> (H x D)]; else NULL */
 } prosper_stats;
 
 /* Create a context for one model and approximation (Sec. 3: BSC_ET(D, H,
@@ -152,8 +154,9 @@ int prosper_destroy(prosper_ctx *ctx);
  * sufficient statistics are summed into *out (overwritten).
  * Y: device N x D FP32.  N >= 0 (N = 0 gives zero statistics).
  * Selection scores: BSC W_h^T y/||W_h||; TSC |W_h^T y|/||W_h||; DSC see
- * prosper_init_dsc; MCA sum_d W_dh y_d / sum_d W_dh; GSC the singleton
- * log-joint log p(e_h, y).  Exact score ties go to the lower h. */
+ * prosper_init_dsc; MCA sum_d W_dh y_d / sum_d W_dh; MMCA sum_d W_dh y_d /
+ * sum_d |W_dh|; GSC the singleton log-joint log p(e_h, y).  Exact score ties
+ * go to the lower h. */
 int prosper_estep(prosper_ctx *ctx, const prosper_params *p, const float *Y, int64_t N,
                   prosper_stats *out, void *stream);
 
@@ -161,7 +164,8 @@ int prosper_estep(prosper_ctx *ctx, const prosper_params *p, const float *Y, int
  * BSC/TSC/DSC/GSC W = A B^{-1} (FP64, blocked Cholesky of B), pi = sum<|s|>/(N H)
  * (TSC: p(+-1) = pi/2; DSC: theta[TH_DSC_P + v] = scal[SC_DSC0 + v]/(N H)),
  * sigma^2 = (sum y^T y - 2 tr(W^T A) + tr(W^T W B))/(N D) with the new W;
- * GSC also mu_h, psi_h; MCA the rho-smoothed-max update of W (clamped >= 1e-6),
+ * GSC also mu_h, psi_h; MCA the rho-smoothed-max update of W (clamped >= 1e-6;
+ * MMCA: the same update on |W| without the clamp),
  * pi as BSC, sigma^2 = sum<||y - f||^2>/(N D).  A unit with B_hh <= 1e-9 N
  * keeps its parameters.  Overwrites p->W, p->theta (and mu, psi) on device. */
 int prosper_mstep(prosper_ctx *ctx, const prosper_stats *st, int64_t N, prosper_params *p,

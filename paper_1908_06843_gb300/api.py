@@ -194,6 +194,17 @@ class MCA_ET(_Model):
         return self._pack(p["Wt"], p["pi"], p["sigma"], rho=self.rho)
 
 
+class MMCA_ET(MCA_ET):
+    """Max-magnitude causes analysis (Table 1, row MMCA): per pixel the active
+    component of largest |W_dh|; signed dictionary."""
+    kind = binding.MMCA
+
+    def standard_init(self, data, seed=0):
+        y = np.asarray(data["y"] if isinstance(data, dict) else data, np.float32)
+        p = synth.init_bsc(y, self.H, seed=seed, pi=0.1, normalise=False)
+        return self._pack(p["Wt"], p["pi"], p["sigma"], rho=self.rho)
+
+
 class GSC_ET(_Model):
     """Gaussian sparse coding, spike-and-slab prior (Table 1, row GSC)."""
     kind = binding.GSC

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-BSC, MCA, GSC, TSC, DSC = 0, 1, 2, 3, 4
+BSC, MCA, GSC, TSC, DSC, MMCA = 0, 1, 2, 3, 4, 5
 FP32, BF16_RESCORE = 0, 1
 TH_PI, TH_SIGMA, TH_RHO, TH_T, TH_DSC_P, THETA_LEN = 0, 1, 2, 3, 4, 8
 SC_F, SC_S1, SC_YY, SC_N, SC_MCA_R2, SC_DSC0, SC_LEN = 0, 1, 2, 3, 4, 5, 8
@@ -163,7 +163,7 @@ class Context:
         st = dict(At=torch.zeros(H, D, **f64), B=torch.zeros(H, H, **f64),
                   scal=torch.zeros(SC_LEN, **f64),
                   gsc=torch.zeros(3 * H, **f64) if self.model == GSC else None,
-                  mca=torch.zeros(2, H, D, **f64) if self.model == MCA else None)
+                  mca=torch.zeros(2, H, D, **f64) if self.model in (MCA, MMCA) else None)
         return st
 
     @staticmethod

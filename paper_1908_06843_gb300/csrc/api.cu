@@ -108,7 +108,7 @@ static int check_stats(const prosper_ctx *c, const prosper_stats *st) {
         set_error("stats: GSC needs gsc[3H]");
         return PROSPER_EINVAL;
     }
-    if (c->model == PROSPER_MCA && !st->mca) {
+    if (max_model(c->model) && !st->mca) {
         set_error("stats: MCA needs mca[2HD]");
         return PROSPER_EINVAL;
     }
@@ -125,10 +125,10 @@ static int estep_begin(prosper_ctx *c, const prosper_params *p, prosper_stats *s
     PROSPER_CUDA_TRY(cudaMemsetAsync(st->scal, 0, sizeof(double) * PROSPER_SC_LEN, s));
     if (c->model == PROSPER_GSC)
         PROSPER_CUDA_TRY(cudaMemsetAsync(st->gsc, 0, sizeof(double) * 3 * H, s));
-    if (c->model == PROSPER_MCA)
+    if (max_model(c->model))
         PROSPER_CUDA_TRY(cudaMemsetAsync(st->mca, 0, sizeof(double) * 2 * H * D, s));
     if (linear_model(c->model)) return launch_bsc_prep(c, p->W, s);
-    if (c->model == PROSPER_MCA) return launch_mca_prep(c, p->W, s);
+    if (max_model(c->model)) return launch_mca_prep(c, p->W, s);
     return launch_gsc_prep(c, p, s);
 }
 
@@ -143,7 +143,7 @@ static int estep_piece(prosper_ctx *c, const prosper_params *p, const float *Y, 
         if (rc) return rc;
         return launch_astat(c, Y, n, st->At, s);
     }
-    if (c->model == PROSPER_MCA)
+    if (max_model(c->model))
         return launch_mca_estep(c, p->W, p->theta, Y, n, st, nullptr, nullptr, nullptr, nullptr,
                                 nullptr, s);
     return launch_gsc_estep(c, p, Y, n, st, nullptr, nullptr, nullptr, nullptr, nullptr, s);
@@ -178,8 +178,8 @@ static int init_common(prosper_ctx **out, int model, int D, int H, int Hprime, i
     const int nK = num_states(Hprime, gamma, m);
     if (model == PROSPER_GSC && gamma > 3) { set_error("GSC: gamma=%d > 3", gamma); return PROSPER_EINVAL; }
     if (model == PROSPER_GSC && H > 32) { set_error("GSC: H=%d > 32", H); return PROSPER_EINVAL; }
-    if ((model == PROSPER_GSC || model == PROSPER_MCA) && D > 256) {
-        set_error("MCA/GSC: D=%d > 256", D);
+    if ((model == PROSPER_GSC || max_model(model)) && D > 256) {
+        set_error("MCA/MMCA/GSC: D=%d > 256", D);
         return PROSPER_EINVAL;
     }
     if (model == PROSPER_GSC && gsc_smem_bytes(D, H, Hprime, nK) > 227 * 1024) {
@@ -187,8 +187,8 @@ static int init_common(prosper_ctx **out, int model, int D, int H, int Hprime, i
                   D, H, Hprime, gamma, gsc_smem_bytes(D, H, Hprime, nK));
         return PROSPER_EINVAL;
     }
-    if (model == PROSPER_MCA && nK > 1024) {
-        set_error("MCA: %d states per point > 1024", nK);
+    if (max_model(model) && nK > 1024) {
+        set_error("MCA/MMCA: %d states per point > 1024", nK);
         return PROSPER_EINVAL;
     }
     // the table-driven state kernel (TSC, DSC, BSC above Hprime 10) packs at
@@ -271,7 +271,7 @@ static int init_common(prosper_ctx **out, int model, int D, int H, int Hprime, i
         if (astat_tc_ok(D, H)) ALLOC(c->apart, (size_t)c->num_sms * H * D);
         ALLOC(c->yy, ch * 2);
     }
-    if (model == PROSPER_MCA) ALLOC(c->mca_logW, (size_t)H * D);
+    if (max_model(model)) ALLOC(c->mca_logW, (size_t)H * D);
     if (model == PROSPER_GSC) {
         int nsub = 0;              // nonempty subsets of at most gamma of the H latents
         double b = 1.0;
@@ -296,7 +296,7 @@ static int init_common(prosper_ctx **out, int model, int D, int H, int Hprime, i
 int prosper_init(prosper_ctx **out, int model, int D, int H, int Hprime, int gamma,
                  int precision, int64_t max_points) {
     if (out) *out = nullptr;
-    if (model < PROSPER_BSC || model > PROSPER_TSC) {
+    if (model < PROSPER_BSC || model > PROSPER_MMCA || model == PROSPER_DSC) {
         set_error(model == PROSPER_DSC ? "DSC contexts are created by prosper_init_dsc"
                                        : "unknown model %d", model);
         return PROSPER_EINVAL;
@@ -446,7 +446,7 @@ static int encode_impl(prosper_ctx *c, const prosper_params *p, const float *Y, 
         }
         return PROSPER_OK;
     }
-    if (c->model == PROSPER_MCA) {
+    if (max_model(c->model)) {
         if ((rc = launch_mca_prep(c, p->W, s))) return rc;
         return launch_mca_estep(c, p->W, p->theta, Y, N, nullptr, sel, s_mean, map_idx, map_p,
                                 logZ, s);

@@ -30,6 +30,8 @@ int num_states(int Hp, int gamma, int m = 1);
 inline bool linear_model(int model) {
     return model == PROSPER_BSC || model == PROSPER_TSC || model == PROSPER_DSC;
 }
+// the max-superposition models (MCA, MMCA) share the MCA kernels
+inline bool max_model(int model) { return model == PROSPER_MCA || model == PROSPER_MMCA; }
 
 #define PROSPER_CUDA_TRY(expr)                                                     \
     do {                                                                           \

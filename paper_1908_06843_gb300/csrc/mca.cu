@@ -1,5 +1,8 @@
 // mca.cu -- Maximal Causes Analysis (Table 1, row MCA: max superposition,
-// Gaussian noise, binary latents, Bernoulli prior) truncated E-step.
+// Gaussian noise, binary latents, Bernoulli prior) truncated E-step, and its
+// signed variant MMCA (Table 1, row MMCA: per pixel the active component of
+// largest magnitude, f_d = W_dh* with h* = argmax_{h in s} |W_dh|, the first
+// in unit order on a tie; scores, logs and smoothed maxima on |W|).
 //
 // One warp per data point; lane l owns the pixels d = l + 32 k (k < DK).
 //   1. Preselection score S_h = sum_d W_dh y_d / sum_d W_dh (reading: the paper
@@ -34,6 +37,7 @@ struct McaArgs {
     const double *theta;
     int64_t N;
     int D, H, Hp, gamma, nK;   // nK = number of states per point
+    int mm;                // 1: MMCA (magnitude max, signed W)
     double *mca;           // 2 H D (estep) or NULL
     double *scal;
     int16_t *sel_out, *map_out;
@@ -50,6 +54,12 @@ __device__ __forceinline__ float fast_lg2(float x) {
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// one step of the superposition carried down the state tree: MCA max(f, w);
+// MMCA the value of larger magnitude (f, the earlier unit, on a tie)
+__device__ __forceinline__ float smax(float f, float w, int mm) {
+    return mm ? (fabsf(w) > fabsf(f) ? w : f) : fmaxf(f, w);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -97,11 +107,12 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
         const float w = A.W[i];
         Ws[i] = w;
         WsT[(i % D) * H + i / D] = w;
-        Ls[i] = w > 0.f ? log2f(w) : -INFINITY;
+        const float aw = A.mm ? fabsf(w) : w;
+        Ls[i] = aw > 0.f ? log2f(aw) : -INFINITY;
     }
     for (int h = tid; h < H; h += MW * 32) {
         float s = 0.f;
-        for (int d = 0; d < D; ++d) s += A.W[(size_t)h * D + d];
+        for (int d = 0; d < D; ++d) s += A.mm ? fabsf(A.W[(size_t)h * D + d]) : A.W[(size_t)h * D + d];
         Rc[h] = s > 0.f ? 1.f / s : 0.f;
     }
     if (SMEM_STATS)
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
                     for (int k = 0; k < DK; ++k) {
                         const int d = lane + 32 * k;
-                        f[k] = fmaxf(f[k], d < D ? Ws[I[j] * D + d] : 0.f);
+                        f[k] = smax(f[k], d < D ? Ws[I[j] * D + d] : 0.f, A.mm);
                     }
                 }
                 visit(mask, f);
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
                 for (int k = 0; k < DK; ++k) {
                     const int d = lane + 32 * k;
-                    f1[k] = fmaxf(f0[k], d < D ? Ws[g1 * D + d] : 0.f);
+                    f1[k] = smax(f0[k], d < D ? Ws[g1 * D + d] : 0.f, A.mm);
                 }
                 visit(1u << i1, f1);
                 for (int i2 = i1 + 1; gamma >= 2 && i2 < Hp; ++i2) {
@@ -242,7 +253,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
                     for (int k = 0; k < DK; ++k) {
                         const int d = lane + 32 * k;
-                        f2[k] = fmaxf(f1[k], d < D ? Ws[g2 * D + d] : 0.f);
+                        f2[k] = smax(f1[k], d < D ? Ws[g2 * D + d] : 0.f, A.mm);
                     }
                     visit((1u << i1) | (1u << i2), f2);
                     for (int i3 = i2 + 1; gamma >= 3 && i3 < Hp; ++i3) {
@@ -253,7 +264,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
                         for (int k = 0; k < DK; ++k) {
                             const int d = lane + 32 * k;
-                            f3[k] = fmaxf(f2[k], d < D ? Ws[g3 * D + d] : 0.f);
+                            f3[k] = smax(f2[k], d < D ? Ws[g3 * D + d] : 0.f, A.mm);
                         }
                         visit((1u << i1) | (1u << i2) | (1u << i3), f3);
                         for (int i4 = i3 + 1; gamma >= 4 && i4 < Hp; ++i4) {
@@ -264,7 +275,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
                             for (int k = 0; k < DK; ++k) {
                                 const int d = lane + 32 * k;
-                                f4[k] = fmaxf(f3[k], d < D ? Ws[g4 * D + d] : 0.f);
+                                f4[k] = smax(f3[k], d < D ? Ws[g4 * D + d] : 0.f, A.mm);
                             }
                             visit((1u << i1) | (1u << i2) | (1u << i3) | (1u << i4), f4);
                             for (int i5 = i4 + 1; gamma >= 5 && i5 < Hp; ++i5) {
@@ -275,7 +286,7 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
                                 for (int k = 0; k < DK; ++k) {
                                     const int d = lane + 32 * k;
-                                    f5[k] = fmaxf(f4[k], d < D ? Ws[g5 * D + d] : 0.f);
+                                    f5[k] = smax(f4[k], d < D ? Ws[g5 * D + d] : 0.f, A.mm);
                                 }
                                 visit((1u << i1) | (1u << i2) | (1u << i3) | (1u << i4) | (1u << i5), f5);
                             }
@@ -454,6 +465,7 @@ int launch_mca_estep(prosper_ctx *c, const float *W, const double *theta, const 
     McaArgs A;
     A.W = W; A.Y = Y; A.theta = theta; A.N = N;
     A.D = c->D; A.H = c->H; A.Hp = c->Hp; A.gamma = c->gamma; A.nK = c->nK;
+    A.mm = c->model == PROSPER_MMCA ? 1 : 0;
     if (c->nK > KMAX) {
         set_error("MCA: %d states per point > %d", c->nK, KMAX);
         return PROSPER_EINVAL;
@@ -465,7 +477,7 @@ int launch_mca_estep(prosper_ctx *c, const float *W, const double *theta, const 
     const bool enc = (st == nullptr);
     const int64_t warps = (N + 3) / 4;     // at least 4 points per warp
     const int grid = (int)std::min<int64_t>((warps + MW - 1) / MW, (int64_t)c->num_sms);
-    TraceScope tr(c, enc ? "mca_encode" : "mca_estep", s);
+    TraceScope tr(c, enc ? (A.mm ? "mmca_encode" : "mca_encode") : (A.mm ? "mmca_estep" : "mca_estep"), s);
     const int dk = (c->D + 31) / 32;
     if (dk <= 1) return mca_dispatch<1>(A, enc, grid, s);
     if (dk <= 2) return mca_dispatch<2>(A, enc, grid, s);

@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(NT) k_theta(const double *__restrict__ scal,
     if (threadIdx.x == 0) {
         theta[PROSPER_TH_PI] = scal[PROSPER_SC_S1] / (Ntot * H);
         double s2;
-        if (model == PROSPER_MCA) {
+        if (model == PROSPER_MCA || model == PROSPER_MMCA) {
             s2 = scal[PROSPER_SC_MCA_R2] / (Ntot * D);
         } else {
             const double ridge = 1e-9 * tr / H;
@@ -392,14 +392,16 @@ __global__ void __launch_bounds__(NT) k_theta(const double *__restrict__ scal,
     }
 }
 
-__global__ void k_mca_w(const double *__restrict__ mca, float *W, int H, int D) {
+// W_dh = sum<A_dh> y_d / sum<A_dh> (kept where the denominator is 0); MCA
+// clamps W >= 1e-6 (its powers need W > 0), MMCA's W is signed
+__global__ void k_mca_w(const double *__restrict__ mca, float *W, int H, int D, int clamp) {
     const int64_t HD = (int64_t)H * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < HD;
          i += (int64_t)gridDim.x * blockDim.x) {
         double num = mca[i], den = mca[HD + i];
         if (den > 0.0) {
             double w = num / den;
-            W[i] = (float)(w < 1e-6 ? 1e-6 : w);
+            W[i] = (float)((clamp && w < 1e-6) ? 1e-6 : w);
         }
     }
 }
@@ -417,9 +419,9 @@ int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_par
                  cudaStream_t s) {
     const int H = c->H, D = c->D;
     const double Ntot = (double)N;
-    if (c->model == PROSPER_MCA) {
+    if (c->model == PROSPER_MCA || c->model == PROSPER_MMCA) {
         TraceScope tr(c, "mstep", s, 2);
-        k_mca_w<<<c->num_sms * 4, 256, 0, s>>>(st->mca, p->W, H, D);
+        k_mca_w<<<c->num_sms * 4, 256, 0, s>>>(st->mca, p->W, H, D, c->model == PROSPER_MCA);
         PROSPER_LAUNCH_CHECK();
         k_theta<<<1, NT, 0, s>>>(st->scal, nullptr, 0, 0, nullptr, nullptr, p->theta, nullptr,
                                  nullptr, H, D, Ntot, c->model, 0, c->d_status);

@@ -105,7 +105,7 @@ static int launch_slot(ServeState *S, Slot &s, int n) {
         if (!rc)
             rc = launch_linear_states(c, p->theta, n, 0, nullptr, s.d_sel, s.d_smean,
                                       g > 0 ? s.d_map : nullptr, nullptr, s.d_mapp, s.d_logz, st);
-    } else if (c->model == PROSPER_MCA) {
+    } else if (max_model(c->model)) {
         rc = launch_mca_estep(c, p->W, p->theta, s.d_y, n, nullptr, s.d_sel, s.d_smean,
                               g > 0 ? s.d_map : nullptr, s.d_mapp, s.d_logz, st);
     } else {

@@ -20,6 +20,7 @@ model list fix the shapes):
 - ``gsc``:      D = 64, H = 32, W ~ N(0, 1)/sqrt(D), b_h ~ Bernoulli(3/32),
                 z_h ~ N(mu_h, psi_h = 0.5) with mu_h ~ U(-1, 1), s = b * z,
                 y = W s + N(0, 0.3^2).
+- ``mmca_bars``: the MCA bars with random signs, |max| superposition.
 - ``discrete``: TSC / DSC data on the Gabor dictionary: s_h takes the value
                 phi_v with probability p_v (else 0), y = W s + N(0, sigma^2)
                 (TSC: values -1, +1 with pi/2 each).
@@ -105,6 +106,21 @@ def mca_bars(N: int = 100_000, seed: int = 1003, pi: float = 0.1, sigma: float =
     H, D = Wt.shape
     S = (g.random((N, H)) < pi).astype(np.float64)
     F = np.max(S[:, :, None] * Wt[None, :, :], axis=1)
+    Y = F + sigma * g.standard_normal((N, D))
+    return dict(Y=Y.astype(np.float32), Wt=Wt, S=S, pi=pi, sigma=sigma)
+
+
+def mmca_bars(N: int = 20_000, seed: int = 1005, pi: float = 0.1, sigma: float = 1.0,
+              side: int = 10, value: float = 8.0):
+    """MMCA data: the bars of ``mca_bars`` with a random sign per bar; per pixel
+    the active bar of largest magnitude (the lower index on a tie) plus noise."""
+    g = rng(seed)
+    Wt = bars_dictionary(side, value) * np.where(g.random(2 * side) < 0.5, -1.0, 1.0)[:, None]
+    H, D = Wt.shape
+    S = (g.random((N, H)) < pi).astype(np.float64)
+    A = np.abs(S[:, :, None] * Wt[None, :, :])                  # N x H x D magnitudes
+    win = np.argmax(A, axis=1)                                   # first maximum: the lower h
+    F = np.where(A.max(axis=1) > 0, Wt[win, np.arange(D)[None, :]], 0.0)
     Y = F + sigma * g.standard_normal((N, D))
     return dict(Y=Y.astype(np.float32), Wt=Wt, S=S, pi=pi, sigma=sigma)
 

@@ -77,7 +77,7 @@ def run_case(orc, model, Y, Wt, pi, sigma, Hp, gamma, precision=0, T=0.0, vals=N
     ref = orc.estep(model, Y32, Wt32, pi, sigma, Hp, gamma, sel_in=sel, **kw, **okw)
     N = len(Y32)
     assert st["scal"][orc.SC_N] == N
-    if model == orc.MCA:        # MCA's statistics: sum <A> y and sum <A> (rho-smoothed max)
+    if model in (orc.MCA, orc.MMCA):   # sum <A> y and sum <A> (rho-smoothed (magnitude) max)
         assert relfro(st["mca"], ref["mca"]) <= REL_AGG, relfro(st["mca"], ref["mca"])
         assert abs(st["scal"][orc.SC_MCA_R2] - ref["scal"][orc.SC_MCA_R2]) <= \
             REL_AGG * abs(ref["scal"][orc.SC_MCA_R2])
@@ -208,6 +208,28 @@ def test_mca_selection_golden_on_gpu(orc):
         out = ctx.encode(P, torch.tensor(y[None, :].astype(np.float32), device="cuda"))
         torch.cuda.synchronize()
         assert out["sel"].cpu().numpy()[0].tolist() == want, (Hp, want)
+
+
+# ---------------------------------------------------------------------- MMCA
+def test_mmca_signed_bars(orc):
+    """MMCA (Table 1 row MMCA: |max| superposition) on signed bars (D = 100,
+    H = 20), H' = 8, gamma = 4 (163 states), N = 1,500: statistics, per-point
+    results and the M-step (no positivity clamp) against the oracle."""
+    d = synth.mmca_bars(N=1500, seed=1019)
+    ctx, st, ref, (W, theta, P) = run_case(orc, orc.MMCA, d["Y"], d["Wt"], 0.1, 1.0, 8, 4, rho=20.0)
+    Wt0 = W.cpu().numpy().astype(np.float64)
+    W2 = orc.mstep(orc.MMCA, 1500, st, Wt0, 0.1, 1.0)[0]
+    stg = {k: (None if v is None else torch.tensor(v, device="cuda")) for k, v in st.items()}
+    ctx.mstep(stg, 1500, P)
+    torch.cuda.synchronize()
+    Wg = W.cpu().numpy()
+    assert relfro(Wg, W2) <= REL_AGG and np.any(Wg < 0)
+
+
+def test_mmca_wide_and_annealed(orc):
+    d = synth.mmca_bars(N=600, seed=1020)
+    run_case(orc, orc.MMCA, d["Y"], d["Wt"], 0.1, 1.0, 12, 3, rho=20.0)
+    run_case(orc, orc.MMCA, d["Y"], d["Wt"], 0.1, 1.0, 8, 3, rho=20.0, T=2.0)
 
 
 # -------------------------------------------------------------- annealing T
