@@ -368,6 +368,9 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
                     lw[j] = ((mk >> j) & 1u) ? Ls[I[j] * D + d] : -INFINITY;
                     lmax = fmaxf(lmax, lw[j]);
                 }
+                // every active |W_dh| is 0 at this pixel: no smoothed-max factor
+                // (2^(rho (lw - lmax)) would be 2^NaN)
+                if (lmax == -INFINITY) continue;
                 float t = 0.f;
 #pragma unroll
                 for (int j = 0; j < HPM; ++j)
