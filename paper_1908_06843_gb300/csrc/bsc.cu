@@ -84,6 +84,15 @@ struct ProjSmem {
     unsigned topk[8][64];     // per-warp selection scratch
 };
 
+// Two FP32 FMAs in one instruction (fma.rn.f32x2, sm_100 and later): each
+// half is rounded exactly as fmaf would round it, so results are unchanged;
+// the FMA instruction count of the projection tile halves.
+__device__ __forceinline__ void ffma2(float &c0, float &c1, float a, float b0, float b1) {
+    asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %2};\n mov.b64 rb, {%3, %4};\n"
+        " mov.b64 rc, {%0, %1};\n fma.rn.f32x2 rc, ra, rb, rc;\n mov.b64 {%0, %1}, rc;\n}\n"
+        : "+f"(c0), "+f"(c1) : "f"(a), "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     const int n = pred ? 16 : 0;   // src-size 0 zero-fills the 16 bytes
@@ -225,7 +234,7 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(yv[i], wv[j], acc[i][j]);
+                for (int j = 0; j < 8; j += 2) ffma2(acc[i][j], acc[i][j + 1], yv[i], wv[j], wv[j + 1]);
         }
         if ((q % nk) != nk - 1) continue;
 
