@@ -328,20 +328,45 @@ __device__ __forceinline__ double widen(float x) {
 // At += sum over the per-CTA partials in CTA order.  The sum is carried as an
 // unevaluated FP32 pair hi + lo (Knuth's TwoSum per addition, error about
 // 2^-44 relative) on the FP32 pipe and widened to FP64 once at the end.
-__global__ void k_reduce_parts(const float *__restrict__ part, int nparts, int64_t HD,
-                               double *__restrict__ At) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < HD;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float hi = 0.f, lo = 0.f;
-#pragma unroll 8
-        for (int p = 0; p < nparts; ++p) {
-            const float b = __ldg(part + (size_t)p * HD + i);
-            const float s = hi + b;
-            const float bb = s - hi;
-            lo += (hi - (s - bb)) + (b - bb);
-            hi = s;
+// Fixed-order sum of the per-CTA partials.  A 256-thread block owns 32 float4
+// groups of elements; its thread (g, q) adds partials q, q + 8, q + 16, ... of
+// group g with TwoSum (every load of a thread is independent, so ~19 are in
+// flight), and thread q = 0 then adds the eight (hi, lo) slices in order q =
+// 0..7: the result does not depend on timing.
+constexpr int RP_SL = 8;     // partial slices per element group
+__global__ void __launch_bounds__(256) k_reduce_parts(const float *__restrict__ part, int nparts,
+                                                      int64_t HD, double *__restrict__ At) {
+    __shared__ float4 shi[RP_SL][32], slo[RP_SL][32];
+    const int g = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int64_t i4 = ((int64_t)blockIdx.x * 32 + g) * 4;     // first element of the group
+    float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+    auto add = [](float &h, float &l, float b) {
+        const float s = h + b;
+        const float bb = s - h;
+        l += (h - (s - bb)) + (b - bb);
+        h = s;
+    };
+    if (i4 < HD) {
+#pragma unroll 4
+        for (int p = q; p < nparts; p += RP_SL) {
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(part + (size_t)p * HD + i4));
+            add(hi.x, lo.x, b.x); add(hi.y, lo.y, b.y); add(hi.z, lo.z, b.z); add(hi.w, lo.w, b.w);
         }
-        At[i] += widen(hi) + widen(lo);
+    }
+    shi[q][g] = hi;
+    slo[q][g] = lo;
+    __syncthreads();
+    if (q == 0 && i4 < HD) {
+        float4 H4 = shi[0][g], L4 = slo[0][g];
+        for (int k = 1; k < RP_SL; ++k) {
+            const float4 h2 = shi[k][g], l2 = slo[k][g];
+            add(H4.x, L4.x, h2.x); add(H4.y, L4.y, h2.y); add(H4.z, L4.z, h2.z); add(H4.w, L4.w, h2.w);
+            L4.x += l2.x; L4.y += l2.y; L4.z += l2.z; L4.w += l2.w;
+        }
+        At[i4] += widen(H4.x) + widen(L4.x);
+        At[i4 + 1] += widen(H4.y) + widen(L4.y);
+        At[i4 + 2] += widen(H4.z) + widen(L4.z);
+        At[i4 + 3] += widen(H4.w) + widen(L4.w);
     }
 }
 
@@ -373,8 +398,8 @@ int finish_astat_tc(prosper_ctx *c, double *At, cudaStream_t s) {
     if (c->apart_pieces == 0) return PROSPER_OK;
     const int64_t HD = (int64_t)c->H * c->D;
     TraceScope tr(c, "astat_tc_reduce", s);
-    k_reduce_parts<<<(int)std::min<int64_t>((HD + 255) / 256, 4 * c->num_sms), 256, 0, s>>>(
-        c->apart, c->num_sms, HD, At);
+    // H D is a multiple of 4 (D % 64 == 0 on this path): one block per 128 elements
+    k_reduce_parts<<<(int)((HD + 127) / 128), 256, 0, s>>>(c->apart, c->num_sms, HD, At);
     PROSPER_LAUNCH_CHECK();
     c->apart_pieces = 0;
     return PROSPER_OK;

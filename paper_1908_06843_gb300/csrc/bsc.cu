@@ -350,6 +350,30 @@ __device__ __forceinline__ float fast_ex2(float x) {
     return y;
 }
 
+// Packed two-lane FP32 arithmetic (add/sub/fma .f32x2, sm_100 and later): each
+// half is rounded exactly as the scalar instruction would round it.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 struct StateArgs {
     const int32_t *sel;
     const float *selp;
@@ -370,9 +394,12 @@ struct StateArgs {
 
 // L(lo) = sum_{j in lo} a_j + sum_{i<j in lo} b_ij and c_u(lo) = a_u + sum_{i in lo} b_iu,
 // branch-free with 0/1 multipliers (fmaf(0, x, s) = s and fmaf(1, x, s) = s + x
-// exactly, so these equal the plain sums), then C[t] = L + sum_{u in t} c_u.
+// exactly, so these equal the plain sums), then C[t] = L + sum_{u in t} c_u,
+// held as pairs CP[k] = (C[2k], C[2k+1]): CP[k] = CP[k minus its lowest bit] +
+// c_{ctz(k)+1} on both halves (packed adds), CP[0] = (L, L + c_0).
 #define PROSPER_LO_TERMS()                                                        \
-    float mk[LBX], C[NT];                                                          \
+    float mk[LBX];                                                                 \
+    float2 CP[NT2];                                                                \
     {                                                                              \
         _Pragma("unroll") for (int i = 0; i < LB; ++i) mk[i] = (float)((lo >> i) & 1); \
         float L = 0.f;                                                             \
@@ -387,15 +414,21 @@ struct StateArgs {
             _Pragma("unroll") for (int i = 0; i < LB; ++i) v = fmaf(mk[i], b[i][LB + u], v); \
             c[u] = v;                                                              \
         }                                                                          \
-        C[0] = L;                                                                  \
-        _Pragma("unroll") for (int t = 1; t < NT; ++t) C[t] = C[t & (t - 1)] + c[cctz(t)]; \
+        CP[0] = make_float2(L, L + c[0]);                                          \
+        _Pragma("unroll") for (int k = 1; k < NT2; ++k) {                          \
+            const float cc = c[cctz(k) + 1];                                       \
+            CP[k] = add2(CP[k & (k - 1)], make_float2(cc, cc));                    \
+        }                                                                          \
     }
+
+// l(t) of the current lo pattern from the packed pairs
+#define PROSPER_L(t) (((t) & 1) ? LP[(t) >> 1].y : LP[(t) >> 1].x)
 
 // Pass 1 body for group K: running maximum.
 #define PROSPER_P1_GROUP(K)                                                        \
     if ((K) <= HB && (K) <= cap) {                                                 \
         _Pragma("unroll") for (int t = 0; t < NT; ++t) {                           \
-            if (cpopc(t) == (K)) m = fmaxf(m, C[t] + M[t]);                        \
+            if (cpopc(t) == (K)) m = fmaxf(m, PROSPER_L(t));                       \
         }                                                                          \
     }
 
@@ -405,15 +438,18 @@ struct StateArgs {
         if ((K) <= cap) {                                                          \
             _Pragma("unroll") for (int t = 0; t < NT; ++t) {                       \
                 if (cpopc(t) == (K)) {                                             \
-                    const float l = C[t] + M[t];                                   \
-                    e[t] = fast_ex2(l - m);                                        \
+                    const float d = ((t) & 1) ? DP[(t) >> 1].y : DP[(t) >> 1].x;   \
+                    const float ev = fast_ex2(d);                                  \
+                    if ((t) & 1) EP[(t) >> 1].y = ev; else EP[(t) >> 1].x = ev;   \
                     const int key = klo + ((cpopc(t) << 16) - crev_hi(t, LB, HP)); \
-                    best = min(best, (l == m) ? key : 0x7fffffff);                 \
+                    best = min(best, (d == 0.f) ? key : 0x7fffffff);               \
                 }                                                                  \
             }                                                                      \
         } else {                                                                   \
             _Pragma("unroll") for (int t = 0; t < NT; ++t)                         \
-                if (cpopc(t) == (K)) e[t] = 0.f;                                   \
+                if (cpopc(t) == (K)) {                                             \
+                    if ((t) & 1) EP[(t) >> 1].y = 0.f; else EP[(t) >> 1].x = 0.f;  \
+                }                                                                  \
         }                                                                          \
     }
 
@@ -432,6 +468,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     constexpr int HB = HP < 5 ? HP : 5;
     constexpr int LB = HP - HB;
     constexpr int NT = 1 << HB;
+    constexpr int NT2 = NT / 2;       // packed pairs of hi patterns (HB >= 1)
     constexpr int NLO = 1 << LB;
     constexpr int LBX = LB > 0 ? LB : 1;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -508,7 +545,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
             b[j][i] = b[i][j];
         }
 
-    float M[NT];
+    float2 MP[NT2];                   // (M[2k], M[2k+1])
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
         float s = 0.f;
@@ -517,7 +554,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
 #pragma unroll
             for (int v = u + 1; v < HB; ++v)
                 if (((t >> u) & 1) && ((t >> v) & 1)) s += b[LB + u][LB + v];
-        M[t] = s;
+        if (t & 1) MP[t >> 1].y = s; else MP[t >> 1].x = s;
     }
 
     // -------- pass 1: maximum log-joint over the valid states
@@ -527,6 +564,9 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
         const int cap = gamma - __popc(lo);
         if (cap < 0) continue;
         PROSPER_LO_TERMS();
+        float2 LP[NT2];
+#pragma unroll
+        for (int k = 0; k < NT2; ++k) LP[k] = add2(CP[k], MP[k]);
         PROSPER_P1_GROUP(0);
         PROSPER_P1_GROUP(1);
         PROSPER_P1_GROUP(2);
@@ -539,7 +579,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     float Z = 0.f;
     float LL[LBX][LBX];
     float LH[LBX][HB];
-    float Gacc[NT];
+    float2 GP[NT2];                   // (Gacc[2k], Gacc[2k+1])
 #pragma unroll
     for (int i = 0; i < LBX; ++i) {
 #pragma unroll
@@ -548,7 +588,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
         for (int u = 0; u < HB; ++u) LH[i][u] = 0.f;
     }
 #pragma unroll
-    for (int t = 0; t < NT; ++t) Gacc[t] = 0.f;
+    for (int k = 0; k < NT2; ++k) GP[k] = make_float2(0.f, 0.f);
     int best = 0x7fffffff;
 
 #pragma unroll 1
@@ -557,7 +597,9 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
         if (cap < 0) continue;
         PROSPER_LO_TERMS();
         const int klo = (__popc(lo) << 16) + 0xFFFF - (int)(__brev((unsigned)lo) >> (32 - HP));
-        float e[NT];
+        float2 DP[NT2], EP[NT2];          // l - m and 2^(l - m), pairs
+#pragma unroll
+        for (int k = 0; k < NT2; ++k) DP[k] = sub2(add2(CP[k], MP[k]), make_float2(m, m));
         PROSPER_P2_GROUP(0);
         PROSPER_P2_GROUP(1);
         PROSPER_P2_GROUP(2);
@@ -565,23 +607,28 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
         PROSPER_P2_GROUP(4);
         PROSPER_P2_GROUP(5);
 #pragma unroll
-        for (int t = 0; t < NT; ++t) Gacc[t] += e[t];
-        // R[u] = sum_{t contains u} e[t] and the total, by pairwise halving in place
+        for (int k = 0; k < NT2; ++k) GP[k] = add2(GP[k], EP[k]);
+        // R[u] = sum_{t contains u} e[t] and the total Zlo, folding the pairs
+        // on the highest hi unit first (packed adds), then the pair itself
         float R[HB];
         float Zlo;
         {
+            int np = NT2;
 #pragma unroll
-            for (int u = 0; u < HB; ++u) {
-                const int half = NT >> (u + 1);
-                float r = 0.f;
+            for (int u = HB - 1; u >= 1; --u) {
+                np >>= 1;
+                float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < half; ++t) {
-                    r += e[2 * t + 1];
-                    e[t] = e[2 * t] + e[2 * t + 1];
+                for (int k = 0; k < NT2 / 2; ++k) {
+                    if (k < np) {
+                        acc = add2(acc, EP[k + np]);
+                        EP[k] = add2(EP[k], EP[k + np]);
+                    }
                 }
-                R[u] = r;
+                R[u] = acc.x + acc.y;
             }
-            Zlo = e[0];
+            R[0] = EP[0].y;
+            Zlo = EP[0].x + EP[0].y;
         }
 #pragma unroll
         for (int i = 0; i < LB; ++i) {
@@ -610,7 +657,7 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
                 float s = 0.f;
 #pragma unroll
                 for (int t = 0; t < NT; ++t)
-                    if (((t >> u) & 1) && ((t >> w) & 1)) s += Gacc[t];
+                    if (((t >> u) & 1) && ((t >> w) & 1)) s += ((t & 1) ? GP[t >> 1].y : GP[t >> 1].x);
                 v = s;
             }
             S2[i][j] = v;
