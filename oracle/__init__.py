@@ -62,6 +62,13 @@ def _load():
             _lib.orc_posterior.argtypes = [i32, i32, i32, i32, i32] + [P] * 14
             _lib.orc_scores.argtypes = [i32, i32, i32] + [P] * 6
             _lib.orc_mstep.argtypes = [i32, i32, i32, dbl] + [P] * 9
+            _lib.orc_trunc_prob.argtypes = [i32, i32, dbl]
+            _lib.orc_trunc_prob.restype = dbl
+            _lib.orc_cut_size.argtypes = [i64, i32, i32, dbl]
+            _lib.orc_cut_size.restype = i64
+            _lib.orc_pi_correction.argtypes = [i32, i32, dbl]
+            _lib.orc_pi_correction.restype = dbl
+            _lib.orc_cut_keep.argtypes = [i64, P, i64, P]
     return _lib
 
 
@@ -235,6 +242,52 @@ def mstep_dsc(model, N, stats, Wt, pi, sigma, vals=None, pvals=None):
         raise ValueError(f"orc_mstep failed ({rc})")
     m = len(vals) if vals is not None else 0
     return Wt, th[0], th[1], th[4:4 + m].copy()
+
+
+def trunc_prob(H, gamma, pi):
+    """P_pi(|s| <= gamma) under the Bernoulli prior."""
+    return _load().orc_trunc_prob(H, gamma, float(pi))
+
+
+def cut_size(N, H, gamma, pi):
+    """N_cut = floor(N P_pi(|s| <= gamma)), at least 1 (ET data-point cut)."""
+    return _load().orc_cut_size(int(N), H, gamma, float(pi))
+
+
+def pi_correction(H, gamma, pi):
+    """H pi / E_pi[|s| : |s| <= gamma]."""
+    return _load().orc_pi_correction(H, gamma, float(pi))
+
+
+def cut_keep(logZ, ncut):
+    """Boolean mask of the points whose log Z reaches the ncut-th largest value."""
+    lz = np.ascontiguousarray(logZ, dtype=np.float64)
+    keep = np.zeros(len(lz), np.uint8)
+    _load().orc_cut_keep(len(lz), _p(lz), int(ncut), _p(keep))
+    return keep.astype(bool)
+
+
+def mstep_cut(model, ncut_kept, stats, Wt, pi, sigma, gamma, mu=None, psi=None):
+    """M-step on the kept points' statistics with ET's pi correction:
+    pi_new = (sum<|s|> / (N_kept H)) * H pi / E_pi[|s| : |s| <= gamma]."""
+    H = np.asarray(Wt).shape[0]
+    W2, pi2, s2, mu2, psi2 = mstep(model, ncut_kept, stats, Wt, pi, sigma, mu, psi)
+    return W2, pi2 * pi_correction(H, gamma, pi), s2, mu2, psi2
+
+
+def estep_cut(model, Y, Wt, pi, sigma, Hp, gamma, sel_in=None, logZ_in=None, **kw):
+    """E-step with ET's data-point cut: the plain E-step gives every point's
+    log Z (or logZ_in, e.g. the values a GPU compared against), the cut keeps
+    the points reaching the N_cut-th largest, and the statistics are the
+    E-step's over the kept points (with their candidate sets).  Returns
+    (statistics of the kept points, keep mask, N_cut)."""
+    full = estep(model, Y, Wt, pi, sigma, Hp, gamma, sel_in=sel_in, **kw)
+    H = np.asarray(Wt).shape[0]
+    ncut = cut_size(len(Y), H, gamma, pi)
+    keep = cut_keep(full["logZ"] if logZ_in is None else logZ_in, ncut)
+    sub = estep(model, np.asarray(Y)[keep], Wt, pi, sigma, Hp, gamma,
+                sel_in=full["sel"][keep], **kw)
+    return sub, keep, ncut
 
 
 def exact_em_free_energy(model, Y, Wt, pi, sigma, rho=0.0, mu=None, psi=None):

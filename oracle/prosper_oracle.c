@@ -700,6 +700,65 @@ int orc_estep(int model, int64_t N, int D, int H, int Hp, int gamma,
 }
 
 /* ------------------------------------------------------------------------
+ * ET's data-point cut (reading of the ET variant the paper's references
+ * describe; Sec. 2 only names truncated posteriors):
+ *   N_cut = floor(N P_pi(|s| <= gamma)),  P_pi(|s| <= gamma) =
+ *           sum_{k <= gamma} C(H,k) pi^k (1 - pi)^(H - k)
+ * (the expected number of points generated by at most gamma causes), and the
+ * M-step uses the points whose log sum_{K_n} p(s, y_n) reaches the N_cut-th
+ * largest value (every point tied with it is kept).  Their sum<|s|> is biased
+ * towards few causes, so pi is corrected by H pi / E_pi[|s| : |s| <= gamma].
+ * ---------------------------------------------------------------------- */
+static double binom_pmf_ratio_sum(int H, int gamma, double pi, double *mean_trunc) {
+    /* w_k = C(H,k) pi^k (1-pi)^(H-k) / (1-pi)^H = C(H,k) (pi/(1-pi))^k */
+    double w = 1.0, sw = 0.0, skw = 0.0;
+    for (int k = 0; k <= gamma && k <= H; ++k) {
+        sw += w;
+        skw += k * w;
+        w *= (double)(H - k) / (k + 1) * pi / (1.0 - pi);
+    }
+    if (mean_trunc) *mean_trunc = skw / sw;
+    return sw;
+}
+
+/* P_pi(|s| <= gamma) */
+double orc_trunc_prob(int H, int gamma, double pi) {
+    if (gamma >= H) return 1.0;                  /* every pattern is kept */
+    return binom_pmf_ratio_sum(H, gamma, pi, NULL) * exp(H * log1p(-pi));
+}
+
+int64_t orc_cut_size(int64_t N, int H, int gamma, double pi) {
+    int64_t n = (int64_t)floor((double)N * orc_trunc_prob(H, gamma, pi));
+    if (n < 1) n = 1;
+    return n > N ? N : n;
+}
+
+/* H pi / E_pi[|s| : |s| <= gamma] (1 when gamma >= H: no truncation) */
+double orc_pi_correction(int H, int gamma, double pi) {
+    if (gamma >= H) return 1.0;
+    double m;
+    binom_pmf_ratio_sum(H, gamma, pi, &m);
+    return m > 0.0 ? H * pi / m : 1.0;
+}
+
+/* keep[n] = 1 for the points whose logZ reaches the ncut-th largest value. */
+int orc_cut_keep(int64_t N, const double *logZ, int64_t ncut, uint8_t *keep) {
+    double *v = malloc(sizeof(double) * (size_t)N);
+    memcpy(v, logZ, sizeof(double) * (size_t)N);
+    /* the ncut-th largest by a plain selection sort of the top ncut (tests only) */
+    for (int64_t i = 0; i < ncut && i < N; ++i) {
+        int64_t b = i;
+        for (int64_t j = i + 1; j < N; ++j) if (v[j] > v[b]) b = j;
+        double t = v[i]; v[i] = v[b]; v[b] = t;
+    }
+    const double thr = v[(ncut < N ? ncut : N) - 1];
+    free(v);
+    int64_t kept = 0;
+    for (int64_t n = 0; n < N; ++n) { keep[n] = logZ[n] >= thr; kept += keep[n]; }
+    return (int)kept;
+}
+
+/* ------------------------------------------------------------------------
  * orc_posterior: the full truncated posterior of ONE data point, for tests.
  * Outputs: sel (Hp), masks (nK), vcodes (nK, TSC/DSC value codes; may be
  * NULL), ell (nK log-joints), q (nK),

@@ -447,6 +447,54 @@ def test_mca_selection_known_answer(orc):
 
 
 # ---------------------------------------------------------------------------
+# ET data-point cut (N_cut and the pi correction; reading, see the oracle)
+# ---------------------------------------------------------------------------
+def test_cut_size_is_binomial_cdf(orc):
+    from scipy.stats import binom
+    for H, gamma, pi in [(10, 3, 0.2), (256, 5, 4 / 256), (20, 0, 0.1), (8, 8, 0.4)]:
+        P = orc.trunc_prob(H, gamma, pi)
+        assert abs(P - binom.cdf(gamma, H, pi)) < 1e-12
+        assert orc.cut_size(100_000, H, gamma, pi) == int(np.floor(100_000 * P))
+
+
+def test_pi_correction_bruteforce(orc):
+    """E_pi[|s| : |s| <= gamma] by enumerating all 2^H binary states."""
+    H, pi = 9, 0.27
+    S = all_states(H)
+    k = S.sum(1)
+    p = pi ** k * (1 - pi) ** (H - k)
+    for gamma in (0, 2, 4, 9):
+        if gamma == 0:
+            continue            # E[|s| : |s| = 0] = 0: no correction defined
+        m = (k[k <= gamma] * p[k <= gamma]).sum() / p[k <= gamma].sum()
+        assert abs(orc.pi_correction(H, gamma, pi) - (H * pi / m if gamma < H else 1.0)) < 1e-12
+    # fixed point: a kept set with exactly the truncated prior's mean restores pi
+    m = (k[k <= 3] * p[k <= 3]).sum() / p[k <= 3].sum()
+    assert abs(m / H * orc.pi_correction(H, 3, pi) - pi) < 1e-14
+
+
+def test_cut_keeps_the_best_explained_points(orc):
+    g = synth.rng(61)
+    lz = g.standard_normal(500)
+    keep = orc.cut_keep(lz, 123)
+    assert keep.sum() == 123 and lz[keep].min() >= lz[~keep].max()
+    lz[[3, 7, 11]] = np.sort(lz)[::-1][122]      # a three-way tie at the boundary: all kept
+    keep = orc.cut_keep(lz, 123)
+    assert keep[[3, 7, 11]].all() and lz[keep].min() >= lz[~keep].max()
+
+
+def test_cut_without_truncation_is_the_plain_estep(orc):
+    """gamma = H' = H: K_n holds every pattern, N_cut = N, nothing is cut."""
+    Y, Wt = _small_bsc(12, H=6, D=9, N=20)
+    sub, keep, ncut = orc.estep_cut(orc.BSC, Y, Wt, 0.3, 0.8, 6, 6)
+    full = orc.estep(orc.BSC, Y, Wt, 0.3, 0.8, 6, 6)
+    assert ncut == 20 and keep.all()
+    np.testing.assert_allclose(sub["At"], full["At"], rtol=1e-13)
+    np.testing.assert_allclose(sub["scal"], full["scal"], rtol=1e-13)
+    assert orc.pi_correction(6, 6, 0.3) == 1.0
+
+
+# ---------------------------------------------------------------------------
 # MMCA (Table 1: |max| superposition, signed dictionary, binary latents)
 # ---------------------------------------------------------------------------
 def brute_logjoint_mmca(y, Wt, pi, sigma):
