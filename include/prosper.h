@@ -160,6 +160,20 @@ int prosper_destroy(prosper_ctx *ctx);
 int prosper_estep(prosper_ctx *ctx, const prosper_params *p, const float *Y, int64_t N,
                   prosper_stats *out, void *stream);
 
+/* ET's data-point cut (a variant of the truncated E-step from the ET
+ * literature the paper builds on; BSC and TSC contexts).  While on, every
+ * prosper_estep runs two passes: the first computes each point's
+ * log sum_{K_n} p(s, y_n); the statistics (At, B, scal including F and the
+ * count scal[PROSPER_SC_N]) are then summed over the points whose FP32 log Z
+ * reaches the N_cut-th largest value, N_cut = floor(N P_pi(|s| <= gamma))
+ * (at least 1; ties at the threshold are all kept).  prosper_mstep then
+ * multiplies the new pi by H pi / E_pi[|s| : |s| <= gamma] at the current pi
+ * (the kept points favour few causes); pass it N = scal[PROSPER_SC_N].
+ * The first pass allocates one float per point on the first call that needs
+ * more room.  Not available with prosper_estep_host.  PROSPER_EINVAL for the
+ * other models. */
+int prosper_set_data_cut(prosper_ctx *ctx, int on);
+
 /* Closed-form M-step ("Model.step", Sec. 3) from statistics of N points:
  * BSC/TSC/DSC/GSC W = A B^{-1} (FP64, blocked Cholesky of B), pi = sum<|s|>/(N H)
  * (TSC: p(+-1) = pi/2; DSC: theta[TH_DSC_P + v] = scal[SC_DSC0 + v]/(N H)),

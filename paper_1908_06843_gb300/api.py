@@ -57,11 +57,13 @@ class _Model:
     kind = binding.BSC
 
     def __init__(self, D, H, Hprime, gamma, precision=binding.FP32, device="cuda",
-                 max_points=1 << 20):
+                 max_points=1 << 20, data_cut=False):
         import torch
         self.D, self.H, self.Hprime, self.gamma = D, H, Hprime, gamma
         self.device = torch.device(device)
         self.ctx = binding.Context(self.kind, D, H, Hprime, gamma, precision, max_points)
+        if data_cut:     # ET's data-point cut (BSC, TSC)
+            self.ctx.set_data_cut(True)
         self._st = None
 
     # -------------------------------------------------------------- helpers

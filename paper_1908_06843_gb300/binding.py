@@ -29,6 +29,7 @@ _I64 = ctypes.c_int64
 ABI = {
     "prosper_init": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _I, _I64]),
     "prosper_init_dsc": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _P, _I64]),
+    "prosper_set_data_cut": (_I, [_P, _I]),
     "prosper_encode_values": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "prosper_destroy": (_I, [_P]),
     "prosper_estep": (_I, [_P, _P, _P, _I64, _P, _P]),
@@ -135,6 +136,10 @@ class Context:
             _check(self.lib.prosper_init(ctypes.byref(h), model, D, H, Hprime, gamma, precision,
                                          int(max_points)), "prosper_init")
         self.h = h
+
+    def set_data_cut(self, on=True):
+        """ET's data-point cut on the following E-steps (prosper_set_data_cut)."""
+        _check(self.lib.prosper_set_data_cut(self.h, 1 if on else 0), "prosper_set_data_cut")
 
     def close(self):
         if getattr(self, "h", None):

@@ -385,6 +385,7 @@ int prosper_destroy(prosper_ctx *c) {
     cudaFree(c->d_hstats);
     cudaFree(c->G); cudaFree(c->rnorm); cudaFree(c->Wd); cudaFree(c->Wb);
     cudaFree(c->mca_logW); cudaFree(c->gsc_tab); cudaFree(c->dsc_tab);
+    cudaFree(c->cut_logz); cudaFree(c->cut_hist); cudaFree(c->cut_state); cudaFree(c->cut_thr);
     cudaFree(c->sel); cudaFree(c->selp); cudaFree(c->yy); cudaFree(c->es); cudaFree(c->apart);
     if (c->h_copy) {
         cudaStreamSynchronize(c->h_copy);
@@ -408,11 +409,36 @@ int prosper_estep(prosper_ctx *c, const prosper_params *p, const float *Y, int64
     if (N < 0 || (N > 0 && !Y)) { set_error("bad Y/N"); return PROSPER_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = estep_begin(c, p, st, s))) return rc;
+    if (c->cut && N > 0) {
+        // data cut: a first pass stores every point's log Z, the threshold of
+        // the N_cut best-explained points follows, and the second pass sums
+        // the statistics of the points that reach it
+        if ((rc = cut_reserve(c, N))) return rc;
+        for (int64_t n0 = 0; n0 < N; n0 += c->chunk) {
+            const int64_t n = std::min<int64_t>(c->chunk, N - n0);
+            if ((rc = launch_linear_proj(c, Y + n0 * c->D, p->W, n, s))) return rc;
+            rc = launch_linear_states(c, p->theta, n, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, c->cut_logz + n0, s);
+            if (rc) return rc;
+        }
+        if ((rc = launch_cut_select(c, p->theta, N, s))) return rc;
+    }
     for (int64_t n0 = 0; n0 < N; n0 += c->chunk) {
         const int64_t n = std::min<int64_t>(c->chunk, N - n0);
+        c->cut_n0 = n0;
         if ((rc = estep_piece(c, p, Y + n0 * c->D, n, st, s))) return rc;
     }
     return estep_end(c, st, s);
+}
+
+int prosper_set_data_cut(prosper_ctx *c, int on) {
+    if (!c) { set_error("ctx is NULL"); return PROSPER_EINVAL; }
+    if (on && c->model != PROSPER_BSC && c->model != PROSPER_TSC) {
+        set_error("data cut: BSC and TSC contexts only");
+        return PROSPER_EINVAL;
+    }
+    c->cut = on ? 1 : 0;
+    return PROSPER_OK;
 }
 
 int prosper_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_params *p,
@@ -477,6 +503,7 @@ int prosper_estep_host(prosper_ctx *c, const prosper_params *p, const float *Y_h
     int rc = check_params(c, p);
     if (rc) return rc;
     if (N < 0 || (N > 0 && !Y_host)) { set_error("bad Y/N"); return PROSPER_EINVAL; }
+    if (c->cut) { set_error("estep_host: the data cut needs the device E-step"); return PROSPER_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     // pieces of 32,768 points (32 MB at D = 256) through NSTAGE device staging
     // buffers: the host link (about 210 GB/s on this part) moves a piece in

@@ -389,6 +389,9 @@ struct StateArgs {
     int16_t *sel_out, *map_out;
     float *smean_out, *mapp_out, *logz_out;
     int64_t n_offset;   // row offset of this piece in the encode outputs
+    // E-step with the data cut: the first pass's log Z of this piece's points
+    // and the threshold; a point below it is left out
+    const float *cut_logz, *cut_thr;
     prosper_ctx *trace_ctx;
 };
 
@@ -699,7 +702,16 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
         return;
     }
 
-    if (valid) {
+    // the data cut leaves a point out of every statistic (its <s> row is
+    // zeroed for sum y<s>^T); the decision reads the FP32 log Z the first
+    // pass stored, so it is the one the threshold was taken on
+    const bool kept = valid && (A.cut_thr == nullptr || A.cut_logz[n] >= *A.cut_thr);
+    if (valid && !kept) {
+        float4 *er = reinterpret_cast<float4 *>(A.es + n * SEL_STRIDE);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) er[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (kept) {
         float4 *er = reinterpret_cast<float4 *>(A.es + n * SEL_STRIDE);
 #pragma unroll
         for (int q = 0; q < NV; ++q)
@@ -731,13 +743,13 @@ __global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
     // the 32 points, the count by ballot), one atomic per warp
     float s1 = 0.f;
     double f = 0.0, y2 = 0.0;
-    if (valid) {
+    if (kept) {
 #pragma unroll
         for (int j = 0; j < HP; ++j) s1 += es[j];
         f = logZ;
         y2 = yy;
     }
-    const unsigned cnt = __popc(__ballot_sync(0xffffffffu, valid));
+    const unsigned cnt = __popc(__ballot_sync(0xffffffffu, kept));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -936,6 +948,8 @@ int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_
     A.scal = st ? st->scal : nullptr;
     A.sel_out = sel_out; A.map_out = map_out; A.smean_out = smean_out; A.mapp_out = mapp_out;
     A.logz_out = logz_out; A.n_offset = n_offset; A.trace_ctx = c;
+    A.cut_thr = (st && c->cut) ? c->cut_thr : nullptr;
+    A.cut_logz = A.cut_thr ? c->cut_logz + c->cut_n0 : nullptr;
     const bool enc = (st == nullptr);
     switch (c->Hp) {
         case 1: return states_dispatch<1>(A, enc, N, s);

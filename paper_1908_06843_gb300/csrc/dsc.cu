@@ -48,6 +48,9 @@ struct DscArgs {
     double *B, *scal;
     int16_t *sel_out, *map_out;
     float *mapv_out, *smean_out, *mapp_out, *logz_out;
+    // E-step with the data cut: the first pass's log Z of this piece's points
+    // and the threshold; a point below it is left out
+    const float *cut_logz, *cut_thr;
 };
 
 __device__ __forceinline__ float fast_ex2(float x) {
@@ -231,8 +234,10 @@ __global__ void __launch_bounds__(XW * 32, 1) k_dsc_states(DscArgs A) {
             continue;
         }
         // E-step statistics: <s> for sum y<s>^T, sum <ss^T> (upper triangle,
-        // I ascending), scalars
-        if (lane < Hp) A.es[n * SEL_STRIDE + lane] = acc[lane * 32];
+        // I ascending), scalars; the data cut leaves a point out of all of them
+        const bool kept = A.cut_thr == nullptr || A.cut_logz[n] >= *A.cut_thr;
+        if (lane < Hp) A.es[n * SEL_STRIDE + lane] = kept ? acc[lane * 32] : 0.f;
+        if (!kept) continue;
         const int npair = Hp * (Hp + 1) / 2;
         for (int base = 0; base < npair; base += 32) {
             const int o = base + lane;
@@ -360,6 +365,8 @@ int launch_dsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_
     A.scal = st ? st->scal : nullptr;
     A.sel_out = sel_out; A.map_out = map_out; A.mapv_out = mapv_out; A.smean_out = smean_out;
     A.mapp_out = mapp_out; A.logz_out = logz_out;
+    A.cut_thr = (st && c->cut) ? c->cut_thr : nullptr;
+    A.cut_logz = A.cut_thr ? c->cut_logz + c->cut_n0 : nullptr;
     const bool enc = (st == nullptr);
     const size_t smem = dsc_smem_bytes(c->Hp, c->dsc_m);
     const void *fn = enc ? (const void *)k_dsc_states<true> : (const void *)k_dsc_states<false>;

@@ -99,6 +99,15 @@ struct prosper_ctx {
     float dsc_vals[3] = {1.f, 0.f, 0.f};   // the nonzero values phi_1 .. phi_m
     int score_mode = 0;         // preselection score: 0 signed, 1 magnitude, 2 negated
 
+    // ET data-point cut (prosper_set_data_cut)
+    int cut = 0;                // 1: statistics from the N_cut best-explained points
+    float *cut_logz = nullptr;  // per-point log Z of the first pass (cut_cap floats)
+    int64_t cut_cap = 0;
+    unsigned *cut_hist = nullptr;     // 2 x 65536 radix-select histograms
+    long long *cut_state = nullptr;   // N_cut, upper bin, count above it
+    float *cut_thr = nullptr;         // the N_cut-th largest log Z
+    int64_t cut_n0 = 0;         // first point of the E-step piece being launched
+
     // per-piece scratch
     int32_t *sel = nullptr;   // chunk x SEL_STRIDE selected latents (ascending)
     float *selp = nullptr;    // chunk x SEL_STRIDE FP32 projections of the selected latents
@@ -155,6 +164,10 @@ int launch_dsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_
 // BSC/TSC/DSC: projection + preselection of a piece of n points, then its
 // states (k_bsc_states for BSC with Hprime <= 10, else the table kernel)
 int launch_linear_proj(prosper_ctx *c, const float *Y, const float *W, int64_t n, cudaStream_t s);
+// ET data-point cut (cut.cu): buffers for N points, and the threshold of the
+// N_cut-th largest log Z in c->cut_logz[0 .. N) into c->cut_thr
+int cut_reserve(prosper_ctx *c, int64_t N);
+int launch_cut_select(prosper_ctx *c, const double *theta, int64_t N, cudaStream_t s);
 int launch_linear_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_offset,
                          prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
                          float *mapv_out, float *mapp_out, float *logz_out, cudaStream_t s);

@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(NT) k_theta(const double *__restrict__ scal,
                                               const double *__restrict__ B,
                                               const double *__restrict__ gsc, double *theta,
                                               float *mu, float *psi, int H, int D, double Ntot,
-                                              int model, int nvals, unsigned *status) {
+                                              int model, int nvals, int cut_gamma,
+                                              unsigned *status) {
     __shared__ double red[NT / 32];
     double pa = 0.0, pi = 0.0, qa = 0.0, x = 0.0, tr = 0.0;
     for (int i = threadIdx.x; i < n1; i += NT) {
@@ -363,7 +364,20 @@ __global__ void __launch_bounds__(NT) k_theta(const double *__restrict__ scal,
     x = block_sum(x, red);
     tr = block_sum(tr, red);
     if (threadIdx.x == 0) {
+        const double pi_old = theta[PROSPER_TH_PI];
         theta[PROSPER_TH_PI] = scal[PROSPER_SC_S1] / (Ntot * H);
+        if (cut_gamma >= 0 && cut_gamma < H) {
+            // data cut: the kept points favour few causes; scale by
+            // H pi / E_pi[|s| : |s| <= gamma] at the current pi
+            double w = 1.0, sw = 0.0, skw = 0.0;
+            for (int k = 0; k <= cut_gamma; ++k) {
+                sw += w;
+                skw += k * w;
+                w *= (double)(H - k) / (k + 1) * pi_old / (1.0 - pi_old);
+            }
+            const double mean = skw / sw;
+            if (mean > 0.0) theta[PROSPER_TH_PI] *= H * pi_old / mean;
+        }
         double s2;
         if (model == PROSPER_MCA || model == PROSPER_MMCA) {
             s2 = scal[PROSPER_SC_MCA_R2] / (Ntot * D);
@@ -424,7 +438,7 @@ int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_par
         k_mca_w<<<c->num_sms * 4, 256, 0, s>>>(st->mca, p->W, H, D, c->model == PROSPER_MCA);
         PROSPER_LAUNCH_CHECK();
         k_theta<<<1, NT, 0, s>>>(st->scal, nullptr, 0, 0, nullptr, nullptr, p->theta, nullptr,
-                                 nullptr, H, D, Ntot, c->model, 0, c->d_status);
+                                 nullptr, H, D, Ntot, c->model, 0, -1, c->d_status);
         PROSPER_LAUNCH_CHECK();
         return PROSPER_OK;
     }
@@ -454,7 +468,7 @@ int launch_mstep(prosper_ctx *c, const prosper_stats *st, int64_t N, prosper_par
     k_t2_inactive<<<n2, NT, 0, s>>>(c->mW, st->B, H, D, Ntot, c->mpart + 3 * n1);
     PROSPER_LAUNCH_CHECK();
     k_theta<<<1, NT, 0, s>>>(st->scal, c->mpart, n1, n2, st->B, st->gsc, p->theta, p->mu, p->psi,
-                             H, D, Ntot, c->model, c->dsc_m, c->d_status);
+                             H, D, Ntot, c->model, c->dsc_m, c->cut ? c->gamma : -1, c->d_status);
     PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }
