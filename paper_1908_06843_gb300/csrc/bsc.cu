@@ -18,6 +18,7 @@
 // with p = W_I^T y.  Kernels work in base 2 (all terms times log2 e).
 #include "internal.cuh"
 #include "topk.cuh"
+#include "f32x2.cuh"
 
 #include <cmath>
 
@@ -25,7 +26,6 @@ namespace prosper {
 
 namespace {
 
-constexpr float kLog2e = 1.4426950408889634f;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kLog2Pi = 1.8378770664093454836;
 
@@ -83,15 +83,6 @@ struct ProjSmem {
     float Ps[PT][PS];         // 66.5 KB
     unsigned topk[8][64];     // per-warp selection scratch
 };
-
-// Two FP32 FMAs in one instruction (fma.rn.f32x2, sm_100 and later): each
-// half is rounded exactly as fmaf would round it, so results are unchanged;
-// the FMA instruction count of the projection tile halves.
-__device__ __forceinline__ void ffma2(float &c0, float &c1, float a, float b0, float b1) {
-    asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %2};\n mov.b64 rb, {%3, %4};\n"
-        " mov.b64 rc, {%0, %1};\n fma.rn.f32x2 rc, ra, rb, rc;\n mov.b64 {%0, %1}, rc;\n}\n"
-        : "+f"(c0), "+f"(c1) : "f"(a), "f"(b0), "f"(b1));
-}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -350,30 +341,6 @@ __device__ __forceinline__ float fast_ex2(float x) {
     return y;
 }
 
-// Packed two-lane FP32 arithmetic (add/sub/fma .f32x2, sm_100 and later): each
-// half is rounded exactly as the scalar instruction would round it.
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-        " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-
 struct StateArgs {
     const int32_t *sel;
     const float *selp;
@@ -466,8 +433,11 @@ struct StateArgs {
 // Pass 1 finds the maximum m; pass 2 forms e = 2^(l - m), the moments and the
 // MAP state (the canonically first state with l == m, found by a min over the
 // key (|s| << 16) + 0xFFFF - bitreverse(s)).
+// The E-step form at H' >= 9 keeps its second-moment table in registers at two
+// CTAs per SM (about 230 registers); at three it spills (A/B at H' = 10,
+// 200,000 points: 0.175 -> 0.160 ms).
 template <int HP, bool ENCODE>
-__global__ void __launch_bounds__(128, 3) k_bsc_states(StateArgs A) {
+__global__ void __launch_bounds__(128, (HP >= 9 && !ENCODE) ? 2 : 3) k_bsc_states(StateArgs A) {
     constexpr int HB = HP < 5 ? HP : 5;
     constexpr int LB = HP - HB;
     constexpr int NT = 1 << HB;

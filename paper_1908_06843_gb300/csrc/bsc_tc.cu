@@ -24,6 +24,7 @@
 //        XOR-swizzled by row so row-wise stores and column reads are conflict-free)
 #include "internal.cuh"
 #include "topk.cuh"
+#include "f32x2.cuh"
 #include "tc.cuh"
 
 #include <cuda_bf16.h>
@@ -70,7 +71,7 @@ __device__ __forceinline__ uint32_t opnd_off(int r, int c, int rows) {
 //   selector warps thread p = TMEM lane p = point p: the H scores of the point
 //                  straight from tensor memory, top-H' (see below), the chosen
 //                  latents ascending into sbuf[i % 2];
-//   rescore warps  one warp per point: the H' selected projections in FP32 from
+//   rescore warps  a half-warp per point: the H' selected projections in FP32 from
 //                  the FP32 Y and W rows, written with the candidate lists.
 // Buffers are handed over with mbarriers (every wait bounded): mma[b] (MMA done:
 // accumulator readable and operand reusable), accfree[b] (selectors done with
@@ -105,7 +106,6 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     unsigned *cand = reinterpret_cast<unsigned *>(sbuf + 2 * TM * 16);       // CMAX x TM keys
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nchunk = D / 8;                 // 16-byte chunks per row
     const int nkb = D / 64;
     const int64_t ntiles = (N + TM - 1) / TM;
     const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
@@ -161,23 +161,26 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
             // waiting for a warp that gave up)
             const bool ok_op = i == 0 || wait_or_abort(&bar_mma[(i - 1) & 1], ((i - 1) >> 1) & 1);
             if (named_sync_or(1, NLD * 32, !ok_op || s_abort)) break;
-            // warp lw converts rows lw + NLD r (r < TM / NLD); eight rows' loads in flight
+            // warp lw converts rows lw + NLD r (r < TM / NLD); eight rows' loads in
+            // flight.  Lane l reads d = 4 l .. 4 l + 3 and 128 + 4 l .. 131 + 4 l
+            // (512 contiguous bytes per instruction) and stores each as 8 bytes
+            // of BF16, half of a 16-byte operand chunk.
+            const int nq4 = D / 4;
             for (int r0 = 0; r0 < TM / NLD; r0 += 8) {
                 float sq[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) sq[k] = 0.f;
-                for (int cb = 0; cb < nchunk; cb += 32) {
-                    const int c = cb + lane;
+                const int u0 = lane, u1 = 32 + lane;
+                {
+                    // rows past N repeat row N - 1 (their scores are never used)
                     float4 v0[8], v1[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const int64_t n = n0 + lw + NLD * (r0 + k);
+                        const int64_t n = min(n0 + lw + NLD * (r0 + k), N - 1);
+                        const float *row = Y + n * D;
                         v0[k] = v1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (c < nchunk && n < N) {
-                            const float *row = Y + n * D + 8 * c;
-                            v0[k] = ldg_hint(row, keep);
-                            v1[k] = ldg_hint(row + 4, keep);
-                        }
+                        if (u0 < nq4) v0[k] = ldg_hint(row + 4 * u0, keep);
+                        if (u1 < nq4) v1[k] = ldg_hint(row + 4 * u1, keep);
                     }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
@@ -187,17 +190,22 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                         q = fmaf(v1[k].x, v1[k].x, q); q = fmaf(v1[k].y, v1[k].y, q);
                         q = fmaf(v1[k].z, v1[k].z, q); q = fmaf(v1[k].w, v1[k].w, q);
                         sq[k] = q;
-                        if (c < nchunk) {
+                        const int r = lw + NLD * (r0 + k);
+                        if (u0 < nq4) {
                             __nv_bfloat162 b0 = __floats2bfloat162_rn(v0[k].x, v0[k].y);
                             __nv_bfloat162 b1 = __floats2bfloat162_rn(v0[k].z, v0[k].w);
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(v1[k].x, v1[k].y);
-                            __nv_bfloat162 b3 = __floats2bfloat162_rn(v1[k].z, v1[k].w);
-                            uint4 pk;
+                            uint2 pk;
                             pk.x = *reinterpret_cast<uint32_t *>(&b0);
                             pk.y = *reinterpret_cast<uint32_t *>(&b1);
-                            pk.z = *reinterpret_cast<uint32_t *>(&b2);
-                            pk.w = *reinterpret_cast<uint32_t *>(&b3);
-                            *reinterpret_cast<uint4 *>(Ysm + opnd_off(lw + NLD * (r0 + k), c, TM)) = pk;
+                            *reinterpret_cast<uint2 *>(Ysm + opnd_off(r, u0 >> 1, TM) + 8 * (u0 & 1)) = pk;
+                        }
+                        if (u1 < nq4) {
+                            __nv_bfloat162 b0 = __floats2bfloat162_rn(v1[k].x, v1[k].y);
+                            __nv_bfloat162 b1 = __floats2bfloat162_rn(v1[k].z, v1[k].w);
+                            uint2 pk;
+                            pk.x = *reinterpret_cast<uint32_t *>(&b0);
+                            pk.y = *reinterpret_cast<uint32_t *>(&b1);
+                            *reinterpret_cast<uint2 *>(Ysm + opnd_off(r, u1 >> 1, TM) + 8 * (u1 & 1)) = pk;
                         }
                     }
                 }
@@ -331,92 +339,96 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
         }
     } else {
         // ------------------------------------------------------------ rescore
-        // One warp per point, lane c holding the 8 values d = 8c .. 8c+7 (D <= 256).
-        // All of a point's rows (RB at a time: every row when Hprime <= 10) are
-        // requested before the first FMA, so each warp keeps up to 10 KB of
-        // gathers in flight.
+        // A half-warp per point, two points per warp: lane l = lane & 15 holds
+        // d = 64 q + 4 l .. 64 q + 4 l + 3 (q < 4, D <= 256) of y and of each
+        // selected W row, so that every load instruction reads 256 contiguous
+        // bytes per point.  Rows are gathered BR at a time, every request of a
+        // batch before its first FMA.  A slot past Hprime holds the sentinel
+        // 0x7fff and reads row H - 1, a quarter past D re-reads the last one
+        // with y = 0, and both products are discarded.  A transposed reduction
+        // over the 16 lanes leaves slot j's projection in lane j of the half.
+        constexpr int BR = 5;
         const int rw = warp - NSEL - NLD;
-        const bool lane_on = lane < nchunk;
+        const int hl = lane & 15, half = lane >> 4;
+        const int nq = D / 64;                            // D is a multiple of 64
+        const int cl = 4 * hl;
         const uint64_t last_use = policy_evict_first();   // y: its last read
         const uint64_t keep = policy_evict_last();        // W rows: read again and again
         for (int i = 0; i < my_tiles; ++i) {
             const int64_t n0 = (blockIdx.x + (int64_t)i * gridDim.x) * TM;
             const int b = i & 1;
             if (!__all_sync(0xffffffffu, wait_or_abort(&bar_selfull[b], (i >> 1) & 1))) break;
-            for (int p = rw; p < TM; p += NRS) {
-                const int64_t n = n0 + p;
-                if (n >= N) break;
+            for (int p0 = 2 * rw; p0 < TM; p0 += 2 * NRS) {
+                if (n0 + p0 >= N) break;                  // warp-uniform
+                const int p = p0 + half;
+                const bool valid = n0 + p < N;
+                const int64_t n = valid ? n0 + p : n0 + p0;
                 const int *hsp = sbuf + (b * TM + p) * 16;
-                float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), y1 = y0;
-                if (lane_on) {
-                    const float *yrow = Y + n * D + 8 * lane;
-                    y0 = ldg_hint(yrow, last_use);
-                    y1 = ldg_hint(yrow + 4, last_use);
-                }
+                float4 yv[4];
+                const float *yrow = Y + n * D + cl;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    yv[q] = q < nq ? ldg_hint(yrow + 64 * q, last_use) : make_float4(0.f, 0.f, 0.f, 0.f);
                 float v[16];
 #pragma unroll
                 for (int r = 0; r < 16; ++r) v[r] = 0.f;
 #pragma unroll
-                for (int rb = 0; rb < 16; rb += RB) {
+                for (int rb = 0; rb < 16; rb += BR) {
                     if (rb < Hp) {   // warp-uniform
-                        float4 w[2 * RB];
+                        float4 w[4 * BR];
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) {
-                            w[2 * r] = w[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (rb + r < 16 && rb + r < Hp && lane_on) {
-                                const float *wrow = Wt + (size_t)hsp[rb + r] * D + 8 * lane;
-                                w[2 * r] = ldg_hint(wrow, keep);
-                                w[2 * r + 1] = ldg_hint(wrow + 4, keep);
+                        for (int r = 0; r < BR; ++r) {
+                            if (rb + r < 16) {
+                                const float *wrow = Wt + (size_t)min(hsp[rb + r], H - 1) * D + cl;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) w[4 * r + q] = ldg_hint(wrow + 64 * min(q, nq - 1), keep);
                             }
                         }
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) {
+                        for (int r = 0; r < BR; ++r) {
                             if (rb + r < 16) {
-                                const float4 w0 = w[2 * r], w1 = w[2 * r + 1];
-                                float sacc = 0.f;
-                                sacc = fmaf(y0.x, w0.x, sacc); sacc = fmaf(y0.y, w0.y, sacc);
-                                sacc = fmaf(y0.z, w0.z, sacc); sacc = fmaf(y0.w, w0.w, sacc);
-                                sacc = fmaf(y1.x, w1.x, sacc); sacc = fmaf(y1.y, w1.y, sacc);
-                                sacc = fmaf(y1.z, w1.z, sacc); sacc = fmaf(y1.w, w1.w, sacc);
-                                v[rb + r] = sacc;
+                                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    const float4 wq = w[4 * r + q], yq = yv[q];
+                                    acc = fma2(make_float2(yq.x, yq.y), make_float2(wq.x, wq.y), acc);
+                                    acc = fma2(make_float2(yq.z, yq.w), make_float2(wq.z, wq.w), acc);
+                                }
+                                v[rb + r] = acc.x + acc.y;
                             }
                         }
                     }
                 }
-                // transposed warp reduction: 16 slots -> lane pair (2k, 2k+1) holds slot jr
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const bool up = (lane & 16) != 0;
+                    const bool up = (hl & 8) != 0;
                     const float send = up ? v[q] : v[q + 8];
-                    const float keep = up ? v[q + 8] : v[q];
-                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                    const float mine = up ? v[q + 8] : v[q];
+                    v[q] = mine + __shfl_xor_sync(0xffffffffu, send, 8);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const bool up = (lane & 8) != 0;
+                    const bool up = (hl & 4) != 0;
                     const float send = up ? v[q] : v[q + 4];
-                    const float keep = up ? v[q + 4] : v[q];
-                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    const float mine = up ? v[q + 4] : v[q];
+                    v[q] = mine + __shfl_xor_sync(0xffffffffu, send, 4);
                 }
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    const bool up = (lane & 4) != 0;
+                    const bool up = (hl & 2) != 0;
                     const float send = up ? v[q] : v[q + 2];
-                    const float keep = up ? v[q + 2] : v[q];
-                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                    const float mine = up ? v[q + 2] : v[q];
+                    v[q] = mine + __shfl_xor_sync(0xffffffffu, send, 2);
                 }
                 {
-                    const bool up = (lane & 2) != 0;
+                    const bool up = (hl & 1) != 0;
                     const float send = up ? v[0] : v[1];
-                    const float keep = up ? v[1] : v[0];
-                    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                    const float mine = up ? v[1] : v[0];
+                    v[0] = mine + __shfl_xor_sync(0xffffffffu, send, 1);
                 }
-                v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-                const int jr = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                               ((lane >> 1) & 1);
-                if ((lane & 1) == 0 && jr < Hp) {
-                    sel_out[n * SEL_STRIDE + jr] = hsp[jr];
-                    selp_out[n * SEL_STRIDE + jr] = v[0];
+                if (valid && hl < Hp) {   // lane hl holds slot hl
+                    sel_out[n * SEL_STRIDE + hl] = hsp[hl];
+                    selp_out[n * SEL_STRIDE + hl] = v[0];
                 }
             }
             __syncwarp();
