@@ -103,7 +103,7 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     unsigned char *Wsm = sbase;
     unsigned char *Ysm = sbase + ((wbytes + 1023) & ~(size_t)1023);
     int *sbuf = reinterpret_cast<int *>(Ysm + (size_t)TM * D * 2);          // 2 x TM x 16 latents
-    unsigned *cand = reinterpret_cast<unsigned *>(sbuf + 2 * TM * 16);       // CMAX x TM keys
+    unsigned *cand = reinterpret_cast<unsigned *>(sbuf + 2 * TM * 16);       // (CMAX + 1) x TM keys
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nkb = D / 64;
@@ -291,17 +291,20 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
                 const unsigned fb = (pre & 0x80000000u) ? (pre & 0x7FFFFFFFu) : ~pre;
                 thr = __uint_as_float(fb);
                 // pass 2: compact the candidates (rounded key >= tau's) into slots
+                // without branches: every key is stored at slot min(cnt, CMAX)
+                // and cnt advances only for a candidate, so a non-candidate is
+                // overwritten by the next candidate or left beyond the count
+                // (slot CMAX only ever holds discarded keys)
                 int cnt = 0;
+                unsigned *cp = cand + p;
 #pragma unroll 1
                 for (int g = 0; g < G; ++g) {
                     float v[16];
                     tmem_ld16_dep(acc + 16 * g, v);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        if (v[j] >= thr) {
-                            if (cnt < CMAX) cand[cnt * TM + p] = packed_key(v[j], 0xFFFFFF00u, 255u - (16 * g + j));
-                            ++cnt;
-                        }
+                        cp[min(cnt, CMAX) * TM] = packed_key(v[j], 0xFFFFFF00u, 255u - (16 * g + j));
+                        cnt += v[j] >= thr ? 1 : 0;
                     }
                 }
                 // overflow in any lane sends the whole warp down the full path
@@ -489,7 +492,7 @@ size_t bf16_smem_bytes(int D, int H) {
     const size_t w = ((size_t)H * D * 2 + 1023) & ~(size_t)1023;
     const size_t y = (size_t)TM * D * 2;                       // BF16 operand of one tile
     const size_t lists = 2 * (size_t)TM * 16 * 4;              // two buffers of candidate lists
-    const size_t cand = (size_t)CMAX * TM * 4;                 // selector candidate slots
+    const size_t cand = (size_t)(CMAX + 1) * TM * 4;           // selector candidate slots (+1 discard)
     return 1024 + w + y + lists + cand;
 }
 
