@@ -21,6 +21,7 @@
 #include "f32x2.cuh"
 
 #include <cmath>
+#include <cuda_bf16.h>
 
 namespace prosper {
 
@@ -30,44 +31,70 @@ constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kLog2Pi = 1.8378770664093454836;
 
 // ------------------------------------------------------------------ prep
-// G[i][j] = sum_d Wt[i][d] Wt[j][d]; 16 x 16 output tile per block.
-__global__ void k_gram(const float *__restrict__ Wt, int H, int D, float *__restrict__ G) {
-    __shared__ float As[16][17], Bs[16][17];
-    int tx = threadIdx.x, ty = threadIdx.y;
-    int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
-    float acc = 0.f;
-    for (int k0 = 0; k0 < D; k0 += 16) {
-        int k = k0 + tx;
-        As[ty][tx] = (i0 + ty < H && k < D) ? Wt[(size_t)(i0 + ty) * D + k] : 0.f;
-        Bs[ty][tx] = (j0 + ty < H && k < D) ? Wt[(size_t)(j0 + ty) * D + k] : 0.f;
-        __syncthreads();
+// The per-iteration constants in one launch.  Block (x, y) computes the 16 x 16
+// tile G[i][j] = sum_d Wt[i][d] Wt[j][d] (i = 16 y + ty, j = 16 x + tx) with the
+// tile's 32 rows of Wt staged in shared memory at once (padded rows, so the 16
+// rows read in one step fall in different banks).  The diagonal blocks also
+// write 1/||W_h|| (0 for a zero row) and, where asked, W in the D x H layout of
+// the FP32 projection (Wd[d][h] = Wt[h][d]) and the BF16 image of the unit-norm
+// rows W_h / ||W_h|| in the tensor-core operand layout of the BF16 projection:
+// K-block kb holds rows h of 128 B (d = 64 kb .. 64 kb + 63), 16-byte chunk c at
+// chunk position c ^ (h & 7).
+__global__ void __launch_bounds__(256) k_prep(const float *__restrict__ Wt, int H, int D,
+                                              float *__restrict__ G, float *__restrict__ rnorm,
+                                              float *__restrict__ Wd, uint16_t *__restrict__ Wb) {
+    extern __shared__ float prep_sm[];
+    __shared__ float s_rn[16];
+    const int P = D + 1;
+    float *As = prep_sm, *Bs = prep_sm + 16 * P;
+    const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+    const bool diag = i0 == j0;                 // block-uniform
+    // 256 columns at a time, all 32 rows' loads in flight before the stores
+    for (int d0 = 0; d0 < D; d0 += 256) {
+        const int d = d0 + threadIdx.x;
+        float va[16], vb[16];
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) acc = fmaf(As[ty][kk], Bs[tx][kk], acc);
-        __syncthreads();
-    }
-    if (i0 + ty < H && j0 + tx < H) G[(size_t)(i0 + ty) * H + j0 + tx] = acc;
-}
-
-__global__ void k_rnorm(const float *__restrict__ G, int H, float *__restrict__ rnorm) {
-    int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h < H) {
-        float g = G[(size_t)h * H + h];
-        rnorm[h] = g > 0.f ? rsqrtf(g) : 0.f;
-    }
-}
-
-// Wd[d][h] = Wt[h][d]
-__global__ void k_transpose(const float *__restrict__ Wt, int H, int D, float *__restrict__ Wd) {
-    __shared__ float t[32][33];
-    int h0 = blockIdx.y * 32, d0 = blockIdx.x * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        int h = h0 + r, d = d0 + threadIdx.x;
-        t[r][threadIdx.x] = (h < H && d < D) ? Wt[(size_t)h * D + d] : 0.f;
+        for (int r = 0; r < 16; ++r) {
+            va[r] = (d < D && i0 + r < H) ? __ldg(Wt + (size_t)(i0 + r) * D + d) : 0.f;
+            vb[r] = (d < D && j0 + r < H && !diag) ? __ldg(Wt + (size_t)(j0 + r) * D + d) : 0.f;
+        }
+        if (d < D) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                As[r * P + d] = va[r];
+                if (!diag) Bs[r * P + d] = vb[r];
+            }
+        }
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        int d = d0 + r, h = h0 + threadIdx.x;
-        if (d < D && h < H) Wd[(size_t)d * H + h] = t[threadIdx.x][r];
+    const float *Bv = diag ? As : Bs;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc = 0.f;
+#pragma unroll 16
+    for (int d = 0; d < D; ++d) acc = fmaf(As[ty * P + d], Bv[tx * P + d], acc);
+    if (i0 + ty < H && j0 + tx < H) G[(size_t)(i0 + ty) * H + j0 + tx] = acc;
+    if (!diag) return;
+    if (tx == ty) {
+        const float rn = acc > 0.f ? rsqrtf(acc) : 0.f;
+        s_rn[ty] = rn;
+        if (i0 + ty < H) rnorm[i0 + ty] = rn;
+    }
+    __syncthreads();
+    if (Wd) {
+        for (int idx = threadIdx.x; idx < 16 * D; idx += 256) {
+            const int d = idx >> 4, r = idx & 15;
+            if (i0 + r < H) Wd[(size_t)d * H + i0 + r] = As[r * P + d];
+        }
+    }
+    if (Wb) {
+        for (int idx = threadIdx.x; idx < 16 * D; idx += 256) {
+            const int r = idx / D, d = idx - r * D, h = i0 + r;
+            if (h >= H) continue;
+            const int kb = d >> 6, ch = (d & 63) >> 3, w = d & 7;
+            const size_t off = (size_t)kb * H * 64 + (size_t)h * 64 + (size_t)((ch ^ (h & 7)) * 8 + w);
+            const __nv_bfloat16 bv = __float2bfloat16_rn(As[r * P + d] * s_rn[r]);
+            Wb[off] = *reinterpret_cast<const uint16_t *>(&bv);
+        }
     }
 }
 
@@ -857,20 +884,12 @@ __global__ void k_symmetrize(double *B, int H) {
 // ================================================================ launchers
 int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
     const int H = c->H, D = c->D;
-    {
-        TraceScope tr(c, "bsc_prep", s, c->Wd ? 3 : 2);
-        dim3 gb(16, 16), gg((H + 15) / 16, (H + 15) / 16);
-        k_gram<<<gg, gb, 0, s>>>(W, H, D, c->G);
-        PROSPER_LAUNCH_CHECK();
-        k_rnorm<<<(H + 255) / 256, 256, 0, s>>>(c->G, H, c->rnorm);
-        PROSPER_LAUNCH_CHECK();
-        if (c->Wd) {
-            dim3 tb(32, 8), tg((D + 31) / 32, (H + 31) / 32);
-            k_transpose<<<tg, tb, 0, s>>>(W, H, D, c->Wd);
-            PROSPER_LAUNCH_CHECK();
-        }
-    }
-    if (c->Wb) return launch_bsc_bf16_prep(c, W, s);
+    const size_t smem = sizeof(float) * 32 * (size_t)(D + 1);
+    if (int rc = ensure_smem_attr((const void *)k_prep, smem)) return rc;
+    TraceScope tr(c, "bsc_prep", s);
+    dim3 gg((H + 15) / 16, (H + 15) / 16);
+    k_prep<<<gg, 256, smem, s>>>(W, H, D, c->G, c->rnorm, c->Wd, c->Wb);
+    PROSPER_LAUNCH_CHECK();
     return PROSPER_OK;
 }
 

@@ -469,23 +469,6 @@ k_bsc_proj_bf16(const float *__restrict__ Y, const float *__restrict__ Wt,
     }
 }
 
-// BF16 image of the unit-norm rows W_h / ||W_h|| (zero rows stay zero), so that
-// the tensor cores produce the preselection scores directly, in the operand
-// layout above: K-block kb holds rows h of 128 B
-// (d = 64 kb .. 64 kb + 63), 16-byte chunk c stored at chunk position c ^ (h & 7).
-__global__ void k_w_image(const float *__restrict__ Wt, const float *__restrict__ rnorm, int H, int D,
-                          uint16_t *__restrict__ img) {
-    const int64_t total = (int64_t)H * D;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int h = (int)(i / D), d = (int)(i % D);
-        const int kb = d >> 6, ch = (d & 63) >> 3, w = d & 7;
-        const size_t off = (size_t)kb * H * 64 + (size_t)h * 64 + (size_t)((ch ^ (h & 7)) * 8 + w);
-        const __nv_bfloat16 b = __float2bfloat16_rn(Wt[i] * rnorm[h]);
-        img[off] = *reinterpret_cast<const uint16_t *>(&b);
-    }
-}
-
 }  // namespace
 
 size_t bf16_smem_bytes(int D, int H) {
@@ -494,13 +477,6 @@ size_t bf16_smem_bytes(int D, int H) {
     const size_t lists = 2 * (size_t)TM * 16 * 4;              // two buffers of candidate lists
     const size_t cand = (size_t)(CMAX + 1) * TM * 4;           // selector candidate slots (+1 discard)
     return 1024 + w + y + lists + cand;
-}
-
-int launch_bsc_bf16_prep(prosper_ctx *c, const float *W, cudaStream_t s) {
-    TraceScope tr(c, "bsc_w_image", s);
-    k_w_image<<<c->num_sms * 2, 256, 0, s>>>(W, c->rnorm, c->H, c->D, c->Wb);
-    PROSPER_LAUNCH_CHECK();
-    return PROSPER_OK;
 }
 
 int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t N, cudaStream_t s) {

@@ -150,7 +150,6 @@ int launch_bsc_prep(prosper_ctx *c, const float *W, cudaStream_t s);
 int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t s);
 int launch_bsc_proj_bf16(prosper_ctx *c, const float *Y, const float *W, int64_t N,
                          cudaStream_t s);
-int launch_bsc_bf16_prep(prosper_ctx *c, const float *W, cudaStream_t s);
 size_t bf16_smem_bytes(int D, int H);
 int launch_bsc_states(prosper_ctx *c, const double *theta, int64_t N, int64_t n_offset,
                       prosper_stats *st, int16_t *sel_out, float *smean_out, int16_t *map_out,
