@@ -6,22 +6,22 @@
 // the preselection score of latent h is W_h^T y / ||W_h||.  Here the N x H
 // score matrix is produced 128 points at a time by one tcgen05.mma chain
 // (M = 128 points, N = H latents, K = D pixels) whose A operand is the Y tile
-// converted to BF16 in shared memory and whose B operand is the BF16 copy of W
-// resident in shared memory for the whole persistent CTA.  The accumulator
-// tile (128 lanes x H columns, FP32) is read back with tcgen05.ld, staged in
-// shared memory 64 points at a time, and every warp takes the top-H' of its
-// points.  The ranking key is the score rounded down to 15 mantissa bits with
-// 255 - h in the low byte (ties, including the ones the rounding makes, go to
-// the lower h); the rounding is far below the BF16 error of the score itself.
-// Each lane sorts its 8 keys, then H' rounds of a warp maximum pop the winners.
-// The H' selected projections are then recomputed in FP32 from the FP32 Y and
-// W, so BF16 only decides which latents are candidates.
+// converted to BF16 in shared memory and whose B operand is the BF16 copy of
+// the unit-norm rows of W, resident in shared memory for the whole persistent
+// CTA.  The accumulator tile (128 lanes x H columns, FP32, two buffers in
+// tensor memory) is read back with tcgen05.ld by the selector threads, one
+// point per thread (TMEM lane = point), which take the top-H' (see the kernel
+// comment).  The ranking key is the score rounded down to 15 mantissa bits
+// with 255 - h in the low byte (ties, including the ones the rounding makes,
+// go to the lower h); the rounding is far below the BF16 error of the score
+// itself.  The H' selected projections are then recomputed in FP32 from the
+// FP32 Y and W rows, so BF16 only decides which latents are candidates.
 //
 // Shared memory (1024-byte aligned, K-major, 128-byte swizzle, 8-row core groups):
-//   W  : D/64 K-blocks, each H rows x 128 B    (H*D*2 bytes, resident)
-//   Y  : D/64 K-blocks, each 128 rows x 128 B  (128*D*2 bytes), reused after the
-//        MMA as the FP32 projection stage P (64 rows x H floats, 16-byte chunks
-//        XOR-swizzled by row so row-wise stores and column reads are conflict-free)
+//   W     : D/64 K-blocks, each H rows x 128 B    (H*D*2 bytes, resident)
+//   Y     : D/64 K-blocks, each 128 rows x 128 B  (128*D*2 bytes, one tile)
+//   lists : two buffers of 128 x 16 candidate latents (selectors -> rescore)
+//   cand  : 33 x 128 candidate keys (selector slots, one of them a discard slot)
 #include "internal.cuh"
 #include "topk.cuh"
 #include "f32x2.cuh"
