@@ -19,6 +19,7 @@
 #include "internal.cuh"
 #include "topk.cuh"
 #include "f32x2.cuh"
+#include "tc.cuh"
 
 #include <cmath>
 #include <cuda_bf16.h>
@@ -104,11 +105,15 @@ constexpr int PK = 32;        // d per k-chunk
 constexpr int PH = 256;       // max H of this kernel
 constexpr int PS = PH + 4;    // padded row of the projection tile in smem
 
+constexpr int PNP = 8;        // product warps (256 threads: 8 x 8 blocks of the tile)
+constexpr int PNR = 4;        // ranking warps
+constexpr unsigned long long kProjWaitNs = 2000000000ull;   // bounded mbarrier wait: 2 s
+
 struct ProjSmem {
     float Ys[2][PK][PT];      // 16 KB  (d-major so a thread reads 8 points with 2 LDS.128)
     float Ws[2][PK][PH];      // 64 KB
-    float Ps[PT][PS];         // 66.5 KB
-    unsigned topk[8][64];     // per-warp selection scratch
+    float Ps[2][PT][PS];      // 133 KB (tile t in Ps[t % 2] while tile t + 1 is multiplied)
+    unsigned topk[PNR][64];   // per-ranking-warp selection scratch
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
@@ -119,15 +124,22 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pr
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// Grid: persistent, one 256-thread CTA per SM.  Thread (tp = tid & 7, th = tid >> 3)
-// accumulates the 8 x 8 block P[tp*8 + i][th*8 + j] of the 64 x 256 tile.  The
-// k-chunks of all tiles form one software pipeline: while chunk q is multiplied,
-// the Y values of chunk q+1 are in flight into registers and its W rows into the
-// other shared-memory stage (cp.async).
+// Grid: persistent, one 384-thread CTA per SM, warp-specialised.  Product
+// thread (tp = tid & 7, th = tid >> 3, tid < 256) accumulates the 8 x 8 block
+// P[tp*8 + i][th*8 + j] of the 64 x 256 tile.  The k-chunks of all tiles form one
+// software pipeline: while chunk q is multiplied, the Y values of chunk q+1 are
+// in flight into registers and its W rows into the other shared-memory stage
+// (cp.async); the product warps meet on named barrier 1 per chunk.  At a tile's
+// end they write its projections to Ps[t % 2] and arrive on full[t % 2]; the
+// four ranking warps take the top-H' of the tile's 64 points (16 each) while the
+// products of the next tile run, then arrive on empty[t % 2], which the product
+// warps wait for before they write that buffer again.  Every wait is bounded;
+// a wait that gives up stops both roles and the CTA writes in-bounds candidate
+// lists for all its points.
 // RMAX: the largest Hprime of the instantiation (10 or 16); the selection
 // rounds are unrolled up to it
 template <int RMAX>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(32 * (PNP + PNR), 1)
 k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
                const float *__restrict__ rnorm, int64_t N, int D, int H, int Hp, int score_mode,
                int32_t *__restrict__ sel_out, float *__restrict__ selp_out,
@@ -156,6 +168,17 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
         kmask[j] = h < H ? 0xFFFFFF00u : 0u;
         klow[j] = h < H ? (unsigned)(255 - h) : 0u;
     }
+    __shared__ uint64_t bar_full[2], bar_empty[2];
+    __shared__ volatile int s_abort;
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(tc::smem_u32(&bar_full[b]), 32 * PNP);
+            tc::mbar_init(tc::smem_u32(&bar_empty[b]), PNR);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
     // Y chunk mapping: thread loads float4 (q4 = idx & 7) of point p = idx >> 3, idx = tid + 256 r
     float4 yreg[2];
@@ -222,120 +245,168 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
         cp_async_commit();
     };
 
-    float acc[8][8];
+    // Top-H' of point p of the tile whose projections are in Ps[pb] (a ranking
+    // warp): H'+1 rounds of the warp maximum over packed keys (24-bit score
+    // prefix, then 255 - h).  When the H'-th and (H'+1)-th winners differ in the
+    // prefix, every latent left out has a smaller exact score than every one
+    // taken, so the set is the exact top-H'; otherwise (scores within 2^-15 of
+    // each other across the boundary, exact ties included) the exact selection
+    // decides.
+    auto select_point = [&](int pb, int p, int64_t n) {
+        unsigned pk[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-
-    if (nq > 0) {
-        load_y(0);
-        load_w(0, 0);
-    }
-    for (int64_t q = 0; q < nq; ++q) {
-        const int st = (int)(q & 1);
-        store_y(st);
-        cp_async_wait_all();
-        __syncthreads();
-        if (q + 1 < nq) {
-            load_y(q + 1);
-            load_w(q + 1, st ^ 1);
+        for (int j = 0; j < 8; ++j) {
+            const float sc = kmask[j] ? sm.Ps[pb][p][lane + 32 * j] * rn[j] : 0.f;
+            pk[j] = packed_key(mag ? fabsf(sc) : sc, kmask[j], klow[j]);
         }
-#pragma unroll 4
-        for (int kk = 0; kk < PK; ++kk) {
-            float4 y0 = *reinterpret_cast<const float4 *>(&sm.Ys[st][kk][tp * 8]);
-            float4 y1 = *reinterpret_cast<const float4 *>(&sm.Ys[st][kk][tp * 8 + 4]);
-            float4 w0 = *reinterpret_cast<const float4 *>(&sm.Ws[st][kk][th * 8]);
-            float4 w1 = *reinterpret_cast<const float4 *>(&sm.Ws[st][kk][th * 8 + 4]);
-            float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-            float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        sort8_desc(pk);
+        int myh = 0x7fffffff;
+        unsigned wlast = 0u, wnext = 0u;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+        for (int r = 0; r <= RMAX; ++r) {
+            if (r <= Hp) {   // warp-uniform
+                const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
+                if (lane == r && r < Hp) myh = 255 - (int)(w & 0xFFu);
+                if (r == Hp - 1) wlast = w;
+                if (r == Hp) wnext = w;
+                if (pk[0] == w) {
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) ffma2(acc[i][j], acc[i][j + 1], yv[i], wv[j], wv[j + 1]);
-        }
-        if ((q % nk) != nk - 1) continue;
-
-        // ---- tile epilogue: projections to shared memory, then preselection
-        const int64_t n0 = (blockIdx.x + (q / nk) * gridDim.x) * PT;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float *row = &sm.Ps[tp * 8 + i][th * 8];
-            *reinterpret_cast<float4 *>(row) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-            *reinterpret_cast<float4 *>(row + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-        }
-        // y^T y of the tile's points: the 8 threads of a point add their slices
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            float q = ysq[r];
-            q += __shfl_xor_sync(0xffffffffu, q, 1);
-            q += __shfl_xor_sync(0xffffffffu, q, 2);
-            q += __shfl_xor_sync(0xffffffffu, q, 4);
-            const int64_t n = n0 + (tid >> 3) + 32 * r;
-            if ((tid & 7) == 0 && n < N) {
-                yy_out[n] = make_float2(q, 0.f);
-                if (!isfinite(q)) atomicOr(status, ST_NONFINITE);
+                    for (int j = 0; j < 7; ++j) pk[j] = pk[j + 1];
+                    pk[7] = 0u;
+                }
             }
-            ysq[r] = 0.f;
         }
-        __syncthreads();
-        for (int i = 0; i < PT / 8; ++i) {
-            const int p = warp * (PT / 8) + i;
-            const int64_t n = n0 + p;
-            if (n >= N) break;
-            // H'+1 rounds of the warp maximum over packed keys (24-bit score
-            // prefix, then 255 - h).  When the H'-th and (H'+1)-th winners differ
-            // in the prefix, every latent left out has a smaller exact score than
-            // every one taken, so the set is the exact top-H'; otherwise (scores
-            // within 2^-15 of each other across the boundary, exact ties included)
-            // the exact selection below decides.
-            unsigned pk[8];
+        if (Hp < H && (wlast >> 8) == (wnext >> 8)) {
+            unsigned key[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float sc = kmask[j] ? sm.Ps[p][lane + 32 * j] * rn[j] : 0.f;
-                pk[j] = packed_key(mag ? fabsf(sc) : sc, kmask[j], klow[j]);
+                int h = lane + 32 * j;
+                const float sc = sm.Ps[pb][p][lane + 32 * j] * rn[j];
+                key[j] = h < H ? score_key(mag ? fabsf(sc) : sc) : 0u;
             }
-            sort8_desc(pk);
-            int myh = 0x7fffffff;
-            unsigned wlast = 0u, wnext = 0u;
+            myh = warp_topk(key, Hp, lane, sm.topk[warp - PNP]);
+        }
+        int rank = 0;
 #pragma unroll
-            for (int r = 0; r <= RMAX; ++r) {
-                if (r <= Hp) {   // warp-uniform
-                    const unsigned w = __reduce_max_sync(0xffffffffu, pk[0]);
-                    if (lane == r && r < Hp) myh = 255 - (int)(w & 0xFFu);
-                    if (r == Hp - 1) wlast = w;
-                    if (r == Hp) wnext = w;
-                    if (pk[0] == w) {
+        for (int r = 0; r < RMAX; ++r) {
+            const int o = __shfl_sync(0xffffffffu, myh, r);
+            rank += (r < Hp && o < myh) ? 1 : 0;
+        }
+        if (lane < Hp) {
+            sel_out[n * SEL_STRIDE + rank] = myh;
+            selp_out[n * SEL_STRIDE + rank] = sm.Ps[pb][p][myh];
+        }
+    };
+
+    if (warp < PNP) {
+        // ------------------------------------------------------ product warps
+        float acc[8][8];
 #pragma unroll
-                        for (int j = 0; j < 7; ++j) pk[j] = pk[j + 1];
-                        pk[7] = 0u;
-                    }
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+        if (nq > 0) {
+            load_y(0);
+            load_w(0, 0);
+        }
+        for (int64_t q = 0; q < nq; ++q) {
+            const int st = (int)(q & 1);
+            store_y(st);
+            cp_async_wait_all();
+            tc::named_sync(1, 32 * PNP);
+            if (q + 1 < nq) {
+                load_y(q + 1);
+                load_w(q + 1, st ^ 1);
+            }
+#pragma unroll 4
+            for (int kk = 0; kk < PK; ++kk) {
+                float4 y0 = *reinterpret_cast<const float4 *>(&sm.Ys[st][kk][tp * 8]);
+                float4 y1 = *reinterpret_cast<const float4 *>(&sm.Ys[st][kk][tp * 8 + 4]);
+                float4 w0 = *reinterpret_cast<const float4 *>(&sm.Ws[st][kk][th * 8]);
+                float4 w1 = *reinterpret_cast<const float4 *>(&sm.Ws[st][kk][th * 8 + 4]);
+                float yv[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+                float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; j += 2) ffma2(acc[i][j], acc[i][j + 1], yv[i], wv[j], wv[j + 1]);
+            }
+            if ((q % nk) != nk - 1) continue;
+
+            // ---- tile end: projections to Ps[t % 2] once the ranking warps are
+            //      done with its previous tile (the same decision in every
+            //      product thread: they share named barrier 1)
+            const int t = (int)(q / nk);
+            const int b = t & 1;
+            bool ok = true;
+            if (t >= 2) ok = tc::mbar_wait(tc::smem_u32(&bar_empty[b]), (uint32_t)(((t - 2) >> 1) & 1), kProjWaitNs);
+            if (tc::named_sync_or(1, 32 * PNP, !ok)) {
+                if (tid == 0) s_abort = 1;
+                break;
+            }
+            const int64_t n0 = (blockIdx.x + (int64_t)t * gridDim.x) * PT;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float *row = &sm.Ps[b][tp * 8 + i][th * 8];
+                *reinterpret_cast<float4 *>(row) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                *reinterpret_cast<float4 *>(row + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            }
+            // y^T y of the tile's points: the 8 threads of a point add their slices
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float yq = ysq[r];
+                yq += __shfl_xor_sync(0xffffffffu, yq, 1);
+                yq += __shfl_xor_sync(0xffffffffu, yq, 2);
+                yq += __shfl_xor_sync(0xffffffffu, yq, 4);
+                const int64_t n = n0 + (tid >> 3) + 32 * r;
+                if ((tid & 7) == 0 && n < N) {
+                    yy_out[n] = make_float2(yq, 0.f);
+                    if (!isfinite(yq)) atomicOr(status, ST_NONFINITE);
                 }
+                ysq[r] = 0.f;
             }
-            if (Hp < H && (wlast >> 8) == (wnext >> 8)) {
-                unsigned key[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    int h = lane + 32 * j;
-                    const float sc = sm.Ps[p][lane + 32 * j] * rn[j];
-                    key[j] = h < H ? score_key(mag ? fabsf(sc) : sc) : 0u;
-                }
-                myh = warp_topk(key, Hp, lane, sm.topk[warp]);
+            tc::mbar_arrive(tc::smem_u32(&bar_full[b]));
+        }
+        cp_async_wait_all();   // no copy outlives the loop (it may have been left early)
+    } else {
+        // ------------------------------------------------------ ranking warps
+        const int rw = warp - PNP;
+        for (int64_t t = 0; t < my_tiles; ++t) {
+            const int b = (int)(t & 1);
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(tc::smem_u32(&bar_full[b]), (uint32_t)((t >> 1) & 1),
+                                                          kProjWaitNs))) {
+                s_abort = 1;
+                break;
             }
-            int rank = 0;
-#pragma unroll
-            for (int r = 0; r < RMAX; ++r) {
-                const int o = __shfl_sync(0xffffffffu, myh, r);
-                rank += (r < Hp && o < myh) ? 1 : 0;
+            const int64_t n0 = (blockIdx.x + t * gridDim.x) * PT;
+            for (int sp = 0; sp < PT / PNR; ++sp) {
+                const int p = rw * (PT / PNR) + sp;
+                if (n0 + p >= N) break;   // warp-uniform
+                select_point(b, p, n0 + p);
             }
-            if (lane < Hp) {
-                sel_out[n * SEL_STRIDE + rank] = myh;
-                selp_out[n * SEL_STRIDE + rank] = sm.Ps[p][myh];
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(tc::smem_u32(&bar_empty[b]));
+        }
+    }
+    __syncthreads();
+    if (s_abort) {
+        // a wait gave up: flag it and give every point of this CTA a valid (if
+        // meaningless) candidate list so that the later kernels stay in bounds
+        if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+        for (int64_t t = 0; t < my_tiles; ++t) {
+            const int64_t n0 = (blockIdx.x + t * gridDim.x) * PT;
+            for (int k = tid; k < PT * SEL_STRIDE; k += 32 * (PNP + PNR)) {
+                const int64_t n = n0 + k / SEL_STRIDE;
+                if (n >= N) continue;
+                const int j = k % SEL_STRIDE;
+                sel_out[n * SEL_STRIDE + j] = j < H ? j : 0;
+                selp_out[n * SEL_STRIDE + j] = 0.f;
+                if (j == 0) yy_out[n] = make_float2(0.f, 0.f);
             }
         }
-        __syncthreads();
     }
 }
 
@@ -904,11 +975,11 @@ int launch_bsc_proj_f32(prosper_ctx *c, const float *Y, int64_t N, cudaStream_t 
     int grid = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms);
     TraceScope tr(c, "bsc_proj_f32", s);
     if (wide)
-        k_bsc_proj_f32<PROSPER_MAX_HPRIME><<<grid, 256, smem, s>>>(
+        k_bsc_proj_f32<PROSPER_MAX_HPRIME><<<grid, 32 * (PNP + PNR), smem, s>>>(
             Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->score_mode, c->sel, c->selp,
             reinterpret_cast<float2 *>(c->yy), c->d_status);
     else
-        k_bsc_proj_f32<BSC_REG_MAX_HPRIME><<<grid, 256, smem, s>>>(
+        k_bsc_proj_f32<BSC_REG_MAX_HPRIME><<<grid, 32 * (PNP + PNR), smem, s>>>(
             Y, c->Wd, c->rnorm, N, c->D, c->H, c->Hp, c->score_mode, c->sel, c->selp,
             reinterpret_cast<float2 *>(c->yy), c->d_status);
     PROSPER_LAUNCH_CHECK();

@@ -61,7 +61,7 @@ constexpr int BSC_REG_MAX_HPRIME = 10;
 
 // Status word bits written by kernels (ctx->d_status).
 constexpr unsigned ST_NONFINITE = 1u;     // a data point had a non-finite y^T y
-constexpr unsigned ST_TC_TIMEOUT = 2u;    // a tensor-core pipeline wait gave up
+constexpr unsigned ST_TC_TIMEOUT = 2u;    // a bounded pipeline wait (mbarrier) gave up
 constexpr unsigned ST_CHOL_FAIL = 4u;     // M-step matrix not positive definite
 
 struct ServeState;  // serve.cu
