@@ -376,8 +376,10 @@ k_bsc_proj_f32(const float *__restrict__ Y, const float *__restrict__ Wd,
         const int rw = warp - PNP;
         for (int64_t t = 0; t < my_tiles; ++t) {
             const int b = (int)(t & 1);
-            if (!__all_sync(0xffffffffu, tc::mbar_wait(tc::smem_u32(&bar_full[b]), (uint32_t)((t >> 1) & 1),
-                                                          kProjWaitNs))) {
+            // a sleeping wait: the ranking warps leave the issue slots to the
+            // product warps until the tile is there
+            if (!__all_sync(0xffffffffu, tc::mbar_wait_sleep(tc::smem_u32(&bar_full[b]), (uint32_t)((t >> 1) & 1),
+                                                                kProjWaitNs))) {
                 s_abort = 1;
                 break;
             }
