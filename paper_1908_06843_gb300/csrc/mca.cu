@@ -350,8 +350,11 @@ __global__ void __launch_bounds__(MW * 32, 1) k_mca_estep(McaArgs A) {
 #pragma unroll
             for (int k = 0; k < DK; ++k) Abar[j][k] = 0.f;
         for (int v = 0; v < nv; ++v) {
+            // a state whose posterior weight is below 2^-32 of the most
+            // probable one's is skipped (warp-uniform): the at most 1024 such
+            // states hold less than 2^-22 of the largest weight together
+            if (ell[v] - m < -32.f) continue;
             const float e = fast_ex2(ell[v] - m);
-            if (e == 0.f) continue;                  // warp-uniform
             const float q = e * invZ;
             const unsigned mk = msk[v];
             R2 += q * (((ell[v] - lpi * (float)__popc(mk)) / -ih) + yy);   // ||y - f||^2
