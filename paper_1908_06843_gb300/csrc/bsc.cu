@@ -2,10 +2,12 @@
 // f = W s, Gaussian noise, binary latents, Bernoulli prior) truncated E-step.
 //
 // Path per call (paper Sec. 2, EM with truncated posteriors):
-//   k_gram / k_transpose      per-iteration constants: G = W^T W, 1/||W_h||, W (D x H)
+//   k_prep                    per-iteration constants in one launch: G = W^T W,
+//                             1/||W_h||, W (D x H), the BF16 unit-norm image
 //   k_bsc_proj_f32            FP32 SIMT projection W^T y_n for all H latents of a
-//                             64-point tile, then top-H' preselection by the score
-//                             W_h^T y / ||W_h|| (ties to the lower h), one warp per point
+//                             64-point tile by 8 product warps, top-H' preselection
+//                             by the score W_h^T y / ||W_h|| (ties to the lower h)
+//                             by 4 ranking warps, one warp per point
 //   k_bsc_states<H'>          one thread per point: every state with <= gamma active
 //                             units among the H' candidates, log-sum-exp, posterior
 //                             moments, MAP; FP64 accumulation of sum <ss^T>, F, ...
