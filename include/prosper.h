@@ -220,7 +220,9 @@ int prosper_encode_values(prosper_ctx *ctx, const prosper_params *p, const float
  * PROSPER_EINVAL.  W (H x D), theta, Y (N x D) and the outputs are device
  * pointers.  All calls share the array: calls whose GPU work overlaps race,
  * so issue them on one stream.  The first call on each device looks up the
- * array's device address; make it before any stream capture. */
+ * array's device address; make it before any stream capture.  Non-finite
+ * input is not reported here (there is no context status word): such a point
+ * gets a non-finite log Z. */
 int prosper_encode_noalloc(int D, int H, int Hprime, int gamma, const float *W,
                            const double *theta, const float *Y, int64_t N, int16_t *sel,
                            float *s_mean, int16_t *map_idx, float *map_p, float *logZ,
