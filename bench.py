@@ -556,20 +556,22 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    # the serving sweep, the secondary workloads and the CPU baseline run at
+    # N = 1 only (at N > 1 the other GPUs would sit idle meanwhile)
     serving = None
-    if not args.no_serve:
+    if not args.no_serve and ws == 1:
         try:
             serving = serve_sweep(torch, Y, Wt)
         except Exception as e:    # reported, not hidden
             serving = {"error": str(e)}
     secondary = None
-    if not args.no_secondary and args.form == "both" and args.points == NPTS:
+    if not args.no_secondary and args.form == "both" and args.points == NPTS and ws == 1:
         secondary = secondary_configs(torch, dev, args.steps, args.warmup)
     head_name = "bf16_rescore" if "value" in forms.get("bf16_rescore", {}) else "fp32"
     head = forms[head_name]
     cpu = None
     error = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:
         n_s, dt, orc_out, orc_m = time_oracle(Y, Wt, args.cpu_seconds, keep=True)
         cpu = {"value": n_s / dt, "unit": "points/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"first {n_s} of the {NPTS} points, one FP64 oracle E-step ({dt:.1f} s)"}
